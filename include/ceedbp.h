@@ -1,0 +1,171 @@
+/*
+ * ceedbp -- matrix-free high-order spectral-element bake-off operators and
+ * Jacobi-PCG on one GB300 (sm_103a).  C ABI.
+ *
+ * The library implements the bake-off problems of "Scalability of
+ * High-Performance PDE Solvers" (Fischer et al.), Sec. 3 and Table 1:
+ *
+ *   BP1  B u = r      scalar, homogeneous Neumann,   q = N+2 Gauss (GL) points
+ *   BP3  A u = r      scalar, homogeneous Dirichlet, q = N+2 GL points
+ *   BP5  A u = r      scalar, homogeneous Dirichlet, q = N+1 GLL points (collocated)
+ *   BP6  A u_i = r_i  three components,  as BP5
+ *
+ * on hexahedral meshes with an iso-parametric map (Sec. 4, Eq. (18)), with the
+ * assembled operator applied matrix-free as w = Q^T A_L Q u (Eq. (21)), the
+ * element operators in the factored form of Eq. (22) (stiffness) or Eq. (34)
+ * (mass) with geometric factors G^e_mm' of Eq. (23), and diagonally
+ * preconditioned CG around them (Sec. 3).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Global vectors hold one value per unique node (and component): FP64,
+ *   layout [nglobal][ncomp] (component fastest), in the caller's node numbering
+ *   (the numbering used by the l2g map given to ceedbp_setup).  Dirichlet
+ *   entries of outputs are zero.
+ * - Pointers named *_dev are device pointers owned by the caller; the library
+ *   never frees them.  Pointers without the suffix are host pointers, read
+ *   during the call only.
+ * - Every call is ordered on the CUDA stream given to ceedbp_setup.  apply
+ *   and mass never synchronise the host; solve synchronises the stream at the
+ *   end of every chunk of iterations to read the convergence state.
+ * - Status codes are returned, never exceptions.  On any code other than
+ *   CEEDBP_OK, ceedbp_last_error(ctx) describes the cause (for setup failures
+ *   with ctx == NULL, ceedbp_last_error(NULL) holds the message of the
+ *   calling thread's last failed setup).
+ * - Context objects are not thread-safe: one host thread at a time per ctx.
+ */
+#ifndef CEEDBP_H
+#define CEEDBP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CEEDBP_OK = 0,
+  CEEDBP_EINVAL = 1,      /* invalid argument (sizes, order, null pointer, bad l2g) */
+  CEEDBP_ENOMEM = 2,      /* device or host allocation failed */
+  CEEDBP_ECUDA = 3,       /* a CUDA runtime call failed */
+  CEEDBP_ENOCONV = 4,     /* solve hit maxit before the tolerance; info and x are filled */
+  CEEDBP_EBREAKDOWN = 5,  /* CG breakdown: p^T A p <= 0 or a non-finite scalar */
+  CEEDBP_EUNSUPPORTED = 6 /* combination of options not built */
+} ceedbp_status;
+
+/* Arithmetic of the operator inside solve/apply. */
+enum {
+  CEEDBP_FP64 = 0,      /* FP64 storage and arithmetic */
+  CEEDBP_FP32 = 1,      /* inner operator: FP32 storage and arithmetic */
+  CEEDBP_BF16STORE = 2  /* inner operator: BF16 storage of u and G, FP32 arithmetic */
+};
+
+typedef struct {
+  int bp;           /* bake-off problem: 1, 3, 5 or 6 (Table 1) */
+  int order;        /* polynomial order N = p, 1..15; p1 = N+1 nodes per direction */
+  int nquad;        /* quadrature points per direction; 0 = the BP's rule (N+2 GL or N+1 GLL) */
+  int64_t nelem;    /* E, number of hexahedral elements */
+  int64_t nglobal;  /* number of unique nodes */
+} ceedbp_params;
+
+/*
+ * Deformed-box mesh helper (Sec. 3: E elements in a tensor-product array;
+ * element map of Eq. (18) with nodes at the GLL points).
+ * Element (ex, ey, ez), id e = ex + Ex (ey + Ey ez); local node (i, j, k),
+ * a = i + p1 (j + p1 k).  Undeformed node x = (ex + (xi_i + 1)/2) / Ex (same
+ * for y, z); every coordinate is then shifted by
+ * amp * sin(pi x) sin(pi y) sin(pi z) evaluated at the undeformed point.
+ * Global id g = I + (N Ex + 1)(J + (N Ey + 1) K), I = ex N + i.
+ * Outputs (host, caller-allocated, may be NULL to skip):
+ *   coords    [E][p1^3][3] doubles,
+ *   l2g       [E][p1^3] int64 global ids,
+ *   dirichlet [nglobal] bytes, 1 on the boundary of the box.
+ * nglobal_out (may be NULL) receives (N Ex + 1)(N Ey + 1)(N Ez + 1).
+ */
+ceedbp_status ceedbp_mesh_box(int Ex, int Ey, int Ez, int order, double amp,
+                              double* coords, int64_t* l2g, uint8_t* dirichlet,
+                              int64_t* nglobal_out);
+
+typedef struct ceedbp_ctx ceedbp_ctx;
+
+/*
+ * Set up an operator context: uploads the mesh, computes the geometric
+ * factors of Eq. (23) (six symmetric components per quadrature point, scaled
+ * by kappa when given) or the mass factors rho_i rho_j rho_k |J| of Eq. (34),
+ * the gather-scatter offsets of Q^T, and the Jacobi diagonal 1/diag(A) (0 on
+ * Dirichlet nodes).
+ *   params     problem description; nglobal must exceed every l2g entry.
+ *   coords     host [E][p1^3][3] nodal coordinates x^e_ijk (Eq. (18)).
+ *   l2g        host [E][p1^3] global ids (the Boolean map Q of Eq. (21)).
+ *   dirichlet  host [nglobal] bytes (1 = homogeneous Dirichlet node) or NULL
+ *              (no Dirichlet nodes; BP1 ignores it).
+ *   kappa      host [E][q^3] coefficient at quadrature points (stiffness
+ *              problems; Eq. (4) with mu = kappa) or NULL for kappa = 1.
+ *   stream     cudaStream_t to order all work on (NULL = legacy default).
+ *   out        receives the context; owns all device memory it allocates.
+ * Errors: EINVAL (bad sizes, order, l2g out of range), ENOMEM, ECUDA.
+ */
+ceedbp_status ceedbp_setup(const ceedbp_params* params, const double* coords,
+                           const int64_t* l2g, const uint8_t* dirichlet,
+                           const double* kappa, void* stream, ceedbp_ctx** out);
+
+/*
+ * w = M A M u (BP3/5/6, M the 0/1 mask of non-Dirichlet nodes) or w = B u
+ * (BP1): the assembled operator Q^T A_L Q of Eq. (21), applied matrix-free
+ * with the element operator of Eq. (22) (or Eq. (34)) and a deterministic
+ * gather-scatter sum over sorted element slots (no floating-point atomics).
+ * u_dev, w_dev: device FP64 [nglobal][ncomp]; they must not overlap.
+ */
+ceedbp_status ceedbp_apply(ceedbp_ctx* ctx, const double* u_dev, double* w_dev);
+
+/*
+ * w = B u with B the mass matrix in the BP's own quadrature (Eq. (34); for
+ * BP5/BP6 the diagonal GLL mass), no mask.  Used to form right-hand sides
+ * b = M B f.  Same layout and ownership as ceedbp_apply.
+ */
+ceedbp_status ceedbp_mass(ceedbp_ctx* ctx, const double* u_dev, double* w_dev);
+
+/* Jacobi preconditioner: dinv_dev[nglobal] receives 1/diag (0 on Dirichlet nodes). */
+ceedbp_status ceedbp_jacobi(ceedbp_ctx* ctx, double* dinv_dev);
+
+typedef struct {
+  double tol;        /* stop at the first iteration with ||r||_2 <= tol ||b||_2 (per component) */
+  int maxit;         /* iteration limit (ENOCONV when reached without convergence) */
+  int fixed_iters;   /* > 0: run exactly this many iterations, ignore tol */
+  int chunk;         /* iterations per launched CUDA graph between host checks; 0 = 32 */
+  int use_graph;     /* 1 = capture chunks in CUDA graphs (default), 0 = plain launches */
+  int x0_nonzero;    /* 1 = x_dev holds an initial guess; 0 = start from x = 0 */
+} ceedbp_solve_opts;
+
+typedef struct {
+  int iters[3];      /* iterations performed, per component */
+  double rel_res[3]; /* final ||r||_2 / ||b||_2 (recursive residual), per component */
+  double res_norm[3];
+  double b_norm[3];
+  double device_ms;  /* time of the iteration loop measured with CUDA events */
+  int status;        /* same as the return value */
+} ceedbp_solve_info;
+
+/*
+ * Jacobi-PCG (Sec. 3) on the assembled system, one independent CG per
+ * component (BP6).  b_dev: device [nglobal][ncomp]; x_dev: device
+ * [nglobal][ncomp], in: initial guess when opts->x0_nonzero, out: solution.
+ * All CG scalars stay on the device; each iteration is two fused kernels plus
+ * one direction update, launched from a captured CUDA graph.
+ * Returns OK, ENOCONV (info filled, x holds the last iterate), EBREAKDOWN.
+ */
+ceedbp_status ceedbp_solve(ceedbp_ctx* ctx, const double* b_dev, double* x_dev,
+                           const ceedbp_solve_opts* opts, ceedbp_solve_info* info);
+
+/* Release every resource owned by ctx (NULL is accepted). */
+ceedbp_status ceedbp_destroy(ceedbp_ctx* ctx);
+
+/* Message for the last failure on ctx (or of this thread's last failed setup when ctx is NULL). */
+const char* ceedbp_last_error(const ceedbp_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CEEDBP_H */

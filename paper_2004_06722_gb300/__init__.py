@@ -1,0 +1,211 @@
+"""ceedbp: GB300-native matrix-free bake-off operators (BP1/BP3/BP5/BP6) and Jacobi-PCG.
+
+Thin Python binding over the C ABI of ``libceedbp.so`` (declared in
+``include/ceedbp.h``).  Every step of the operator and the solver runs in the
+library's CUDA kernels; this module only marshals arguments.  PyTorch supplies
+device memory and the CUDA stream.  There is no CPU fallback: importing the
+binding without the built library, or calling it without a CUDA device, raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libceedbp.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ENOCONV, EBREAKDOWN, EUNSUPPORTED = range(7)
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "EBREAKDOWN", 6: "EUNSUPPORTED"}
+FP64, FP32, BF16STORE = 0, 1, 2
+
+
+class CeedbpError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("bp", ctypes.c_int), ("order", ctypes.c_int), ("nquad", ctypes.c_int),
+                ("nelem", ctypes.c_int64), ("nglobal", ctypes.c_int64)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("maxit", ctypes.c_int), ("fixed_iters", ctypes.c_int),
+                ("chunk", ctypes.c_int), ("use_graph", ctypes.c_int), ("x0_nonzero", ctypes.c_int)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int * 3), ("rel_res", ctypes.c_double * 3),
+                ("res_norm", ctypes.c_double * 3), ("b_norm", ctypes.c_double * 3),
+                ("device_ms", ctypes.c_double), ("status", ctypes.c_int)]
+
+    def as_dict(self, ncomp: int) -> dict:
+        return {"iters": list(self.iters[:ncomp]), "rel_res": list(self.rel_res[:ncomp]),
+                "res_norm": list(self.res_norm[:ncomp]), "b_norm": list(self.b_norm[:ncomp]),
+                "device_ms": self.device_ms, "status": STATUS_NAMES.get(self.status, self.status)}
+
+
+_P = ctypes.c_void_p
+_SIGS = {
+    "ceedbp_mesh_box": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                       _P, _P, _P, ctypes.POINTER(ctypes.c_int64)]),
+    "ceedbp_setup": (ctypes.c_int, [ctypes.POINTER(Params), _P, _P, _P, _P, _P, ctypes.POINTER(_P)]),
+    "ceedbp_apply": (ctypes.c_int, [_P, _P, _P]),
+    "ceedbp_mass": (ctypes.c_int, [_P, _P, _P]),
+    "ceedbp_jacobi": (ctypes.c_int, [_P, _P]),
+    "ceedbp_solve": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo)]),
+    "ceedbp_destroy": (ctypes.c_int, [_P]),
+    "ceedbp_last_error": (ctypes.c_char_p, [_P]),
+}
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libceedbp.so (built by ``__graft_entry__.build()``); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"ceedbp library not built: {path} is missing (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int, ctx=None):
+    if status != OK:
+        msg = load_library().ceedbp_last_error(ctx)
+        raise CeedbpError(status, msg.decode() if msg else "")
+
+
+def _ptr(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def mesh_box(Ex: int, Ey: int, Ez: int, order: int, amp: float = 0.05):
+    """Deformed-box mesh from the library (coords [E, p1^3, 3], l2g [E, p1^3], dirichlet [n_g])."""
+    lib = load_library()
+    p1 = order + 1
+    E = Ex * Ey * Ez
+    ng = ctypes.c_int64(0)
+    _check(lib.ceedbp_mesh_box(Ex, Ey, Ez, order, amp, None, None, None, ctypes.byref(ng)))
+    coords = np.empty((E, p1 ** 3, 3), dtype=np.float64)
+    l2g = np.empty((E, p1 ** 3), dtype=np.int64)
+    dirichlet = np.empty(ng.value, dtype=np.uint8)
+    _check(lib.ceedbp_mesh_box(Ex, Ey, Ez, order, amp, _ptr(coords), _ptr(l2g), _ptr(dirichlet), None))
+    return coords, l2g, dirichlet
+
+
+class Operator:
+    """One bake-off problem on the GPU: ceedbp_setup / apply / mass / solve / destroy."""
+
+    def __init__(self, bp: int, order: int, coords: np.ndarray, l2g: np.ndarray, dirichlet: np.ndarray | None,
+                 kappa: np.ndarray | None = None, stream=None, device=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("ceedbp needs a CUDA device; there is no CPU path")
+        self.lib = load_library()
+        self.device = torch.device("cuda") if device is None else torch.device(device)
+        # a dedicated stream: CUDA graphs cannot be captured on the legacy default stream
+        self.stream = torch.cuda.Stream(self.device) if stream is None else stream
+        self.bp, self.order = bp, order
+        self.ncomp = 3 if bp == 6 else 1
+        coords = np.ascontiguousarray(coords, dtype=np.float64)
+        l2g = np.ascontiguousarray(l2g, dtype=np.int64)
+        self.nelem = coords.shape[0]
+        self.nglobal = int(dirichlet.shape[0]) if dirichlet is not None else int(l2g.max()) + 1
+        dirichlet = None if dirichlet is None else np.ascontiguousarray(dirichlet, dtype=np.uint8)
+        kappa = None if kappa is None else np.ascontiguousarray(kappa, dtype=np.float64)
+        prm = Params(bp, order, 0, self.nelem, self.nglobal)
+        ctx = ctypes.c_void_p()
+        cur = torch.cuda.current_stream(self.device)
+        self.stream.wait_stream(cur)
+        st = self.lib.ceedbp_setup(ctypes.byref(prm), _ptr(coords), _ptr(l2g), _ptr(dirichlet), _ptr(kappa),
+                                   ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(ctx))
+        _check(st, None)
+        self.ctx = ctx
+
+    @classmethod
+    def box(cls, bp: int, Ex: int, Ey: int, Ez: int, order: int, amp: float = 0.05, kappa=None, **kw):
+        coords, l2g, dirichlet = mesh_box(Ex, Ey, Ez, order, amp)
+        op = cls(bp, order, coords, l2g, dirichlet, kappa=kappa, **kw)
+        op.dims = (Ex, Ey, Ez)
+        op.coords = coords
+        return op
+
+    def _vec(self, v):
+        import torch
+        if not (v.is_cuda and v.dtype == torch.float64 and v.is_contiguous()):
+            raise ValueError("vectors must be contiguous float64 CUDA tensors")
+        if v.numel() != self.nglobal * self.ncomp:
+            raise ValueError(f"vector has {v.numel()} entries, expected {self.nglobal * self.ncomp}")
+        return ctypes.c_void_p(v.data_ptr())
+
+    def empty(self):
+        import torch
+        shape = (self.nglobal,) if self.ncomp == 1 else (self.nglobal, 3)
+        return torch.empty(shape, dtype=torch.float64, device=self.device)
+
+    def _enter(self):
+        import torch
+        cur = torch.cuda.current_stream(self.device)
+        if cur.cuda_stream != self.stream.cuda_stream:
+            self.stream.wait_stream(cur)
+        return cur
+
+    def _leave(self, cur):
+        if cur.cuda_stream != self.stream.cuda_stream:
+            cur.wait_stream(self.stream)
+
+    def _call(self, fn, *args):
+        cur = self._enter()
+        try:
+            st = fn(self.ctx, *args)
+        finally:
+            self._leave(cur)
+        return st
+
+    def apply(self, u, out=None):
+        w = self.empty() if out is None else out
+        _check(self._call(self.lib.ceedbp_apply, self._vec(u), self._vec(w)), self.ctx)
+        return w
+
+    def mass(self, u, out=None):
+        w = self.empty() if out is None else out
+        _check(self._call(self.lib.ceedbp_mass, self._vec(u), self._vec(w)), self.ctx)
+        return w
+
+    def jacobi(self):
+        import torch
+        d = torch.empty(self.nglobal, dtype=torch.float64, device=self.device)
+        _check(self._call(self.lib.ceedbp_jacobi, ctypes.c_void_p(d.data_ptr())), self.ctx)
+        return d
+
+    def solve(self, b, x=None, tol: float = 1e-8, maxit: int = 10000, fixed_iters: int = 0, chunk: int = 32,
+              use_graph: bool = True, x0=False, raise_on_noconv: bool = True):
+        x = self.empty() if x is None else x
+        opts = SolveOpts(tol, maxit, fixed_iters, chunk, int(use_graph), int(bool(x0)))
+        info = SolveInfo()
+        st = self._call(self.lib.ceedbp_solve, self._vec(b), self._vec(x), ctypes.byref(opts), ctypes.byref(info))
+        if st != OK and (raise_on_noconv or st != ENOCONV):
+            _check(st, self.ctx)
+        return x, info.as_dict(self.ncomp)
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None and self.ctx.value:
+            self.lib.ceedbp_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,432 @@
+// C ABI of ceedbp: context setup, operator apply, mass, Jacobi-PCG solve.
+// The entry points are declared and documented in include/ceedbp.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace ceedbp {
+cudaError_t launch_elem_bp1(const DeviceMesh& m, const ElemArgs& a, cudaStream_t s);
+cudaError_t launch_elem_bp3(const DeviceMesh& m, const ElemArgs& a, cudaStream_t s);
+cudaError_t launch_elem_bp5(const DeviceMesh& m, const ElemArgs& a, cudaStream_t s);
+cudaError_t launch_elem_bp6(const DeviceMesh& m, const ElemArgs& a, cudaStream_t s);
+int elem_blocks_bp1(const DeviceMesh& m);
+int elem_blocks_bp3(const DeviceMesh& m);
+int elem_blocks_bp5(const DeviceMesh& m);
+int elem_blocks_bp6(const DeviceMesh& m);
+
+cudaError_t launch_elem(const DeviceMesh& m, int kind, const ElemArgs& a, cudaStream_t s) {
+  if (m.colloc && kind == kStiff) return m.ncomp == 3 ? launch_elem_bp6(m, a, s) : launch_elem_bp5(m, a, s);
+  if (!m.colloc && kind == kStiff && m.ncomp == 1) return launch_elem_bp3(m, a, s);
+  if (!m.colloc && kind == kMass && m.ncomp == 1) return launch_elem_bp1(m, a, s);
+  return cudaErrorInvalidValue;
+}
+
+int elem_blocks(const DeviceMesh& m) {
+  // stiffness and mass instantiations of one (p1, q) share the block shape
+  if (m.colloc) return m.ncomp == 3 ? elem_blocks_bp6(m) : elem_blocks_bp5(m);
+  return elem_blocks_bp3(m);
+}
+}  // namespace ceedbp
+
+using namespace ceedbp;
+
+struct GraphEntry {
+  double* x;
+  int n;
+  cudaGraphExec_t exec;
+};
+
+struct ceedbp_ctx {
+  ceedbp_params prm{};
+  int ncomp = 1, p1 = 0, q = 0, op_kind = kStiff;
+  bool colloc = false;
+  cudaStream_t stream = nullptr;
+  DeviceMesh mesh{};
+  int* d_l2g = nullptr;
+  int* d_off = nullptr;
+  int* d_slots = nullptr;
+  double* d_basis = nullptr;
+  double* d_G = nullptr;
+  double* d_Mq = nullptr;
+  double* d_dinv = nullptr;
+  double* d_mdiag = nullptr;
+  double* d_wl = nullptr;
+  double* d_r = nullptr;
+  double* d_p = nullptr;
+  double* d_ax = nullptr;
+  double* d_part_apply = nullptr;
+  double* d_part_vec = nullptr;
+  SolveState* d_state = nullptr;
+  SolveState* h_state = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::vector<GraphEntry> graphs;
+  std::string err;
+};
+
+namespace {
+
+thread_local std::string g_setup_error;
+
+ceedbp_status fail(ceedbp_ctx* c, ceedbp_status st, const std::string& msg) {
+  if (c) c->err = msg;
+  else g_setup_error = msg;
+  return st;
+}
+
+ceedbp_status cuda_fail(ceedbp_ctx* c, cudaError_t e, const char* what) {
+  std::string msg = std::string(what) + ": " + cudaGetErrorString(e);
+  return fail(c, e == cudaErrorMemoryAllocation ? CEEDBP_ENOMEM : CEEDBP_ECUDA, msg);
+}
+
+#define CK(ctx, call)                                        \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+  return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (count ? count : 1));
+}
+
+void release(ceedbp_ctx* c) {
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+  c->graphs.clear();
+  void* ptrs[] = {c->d_l2g, c->d_off, c->d_slots, c->d_basis, c->d_G, c->d_Mq, c->d_dinv, c->d_mdiag,
+                  c->d_wl, c->d_r, c->d_p, c->d_ax, c->d_part_apply, c->d_part_vec, c->d_state};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (c->h_state) cudaFreeHost(c->h_state);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+}
+
+ceedbp_status setup_impl(ceedbp_ctx* c, const double* coords, const int64_t* l2g, const uint8_t* dirichlet,
+                         const double* kappa) {
+  const ceedbp_params& P = c->prm;
+  if (P.bp != 1 && P.bp != 3 && P.bp != 5 && P.bp != 6) return fail(c, CEEDBP_EUNSUPPORTED, "bp must be 1, 3, 5 or 6");
+  if (P.order < 1 || P.order > kMaxOrder) return fail(c, CEEDBP_EINVAL, "order must be in 1..15");
+  if (P.nelem < 1 || P.nglobal < 1) return fail(c, CEEDBP_EINVAL, "nelem and nglobal must be positive");
+  if (!coords || !l2g) return fail(c, CEEDBP_EINVAL, "coords and l2g are required");
+  const bool gll_quad = (P.bp == 5 || P.bp == 6);
+  const int p1 = P.order + 1;
+  const int qdef = gll_quad ? p1 : P.order + 2;
+  if (P.nquad != 0 && P.nquad != qdef) return fail(c, CEEDBP_EUNSUPPORTED, "only the BP's own quadrature is built");
+  Basis1D basis;
+  std::string berr;
+  if (!build_basis(P.order, qdef, gll_quad, &basis, &berr)) return fail(c, CEEDBP_EINVAL, berr);
+  c->p1 = p1;
+  c->q = qdef;
+  c->colloc = gll_quad;
+  c->ncomp = P.bp == 6 ? 3 : 1;
+  c->op_kind = P.bp == 1 ? kMass : kStiff;
+  const int64_t P3 = int64_t(p1) * p1 * p1, Q3 = int64_t(qdef) * qdef * qdef;
+  const int64_t nloc = P.nelem * P3;
+  if (nloc >= (int64_t(1) << 31) || P.nglobal >= (int64_t(1) << 31) - 1)
+    return fail(c, CEEDBP_EINVAL, "problem too large for 32-bit local indices (E p1^3 and nglobal must stay below 2^31)");
+  const bool masked = P.bp != 1 && dirichlet != nullptr;
+
+  // ---- host: encoded l2g, CSR of local slots per global node (counting sort, slots ascending)
+  std::vector<int> hl2g(nloc), hoff(P.nglobal + 1, 0), hslots(nloc);
+  for (int64_t s = 0; s < nloc; ++s) {
+    const int64_t g = l2g[s];
+    if (g < 0 || g >= P.nglobal) return fail(c, CEEDBP_EINVAL, "l2g entry out of range [0, nglobal)");
+    const bool dir = masked && dirichlet[g];
+    hl2g[s] = dir ? -int(g) - 1 : int(g);
+    hoff[g + 1] += 1;
+  }
+  for (int64_t g = 0; g < P.nglobal; ++g) hoff[g + 1] += hoff[g];
+  {
+    std::vector<int> fill(hoff.begin(), hoff.end() - 1);
+    for (int64_t s = 0; s < nloc; ++s) hslots[fill[l2g[s]]++] = int(s);
+  }
+  if (masked)
+    for (int64_t g = 0; g < P.nglobal; ++g)
+      if (dirichlet[g]) hoff[g] = int(unsigned(hoff[g]) | 0x80000000u);
+
+  std::vector<double> hb(basis_doubles(p1, qdef));
+  std::copy(basis.J.begin(), basis.J.end(), hb.begin());
+  std::copy(basis.Dh.begin(), basis.Dh.end(), hb.begin() + size_t(qdef) * p1);
+  std::copy(basis.Dq.begin(), basis.Dq.end(), hb.begin() + 2 * size_t(qdef) * p1);
+  std::copy(basis.w.begin(), basis.w.end(), hb.begin() + 2 * size_t(qdef) * p1 + size_t(qdef) * qdef);
+
+  const int nc = c->ncomp;
+  const int64_t n = P.nglobal;
+  CK(c, dalloc(&c->d_l2g, nloc));
+  CK(c, dalloc(&c->d_off, n + 1));
+  CK(c, dalloc(&c->d_slots, nloc));
+  CK(c, dalloc(&c->d_basis, hb.size()));
+  if (c->op_kind == kStiff) CK(c, dalloc(&c->d_G, size_t(P.nelem) * 6 * Q3));
+  CK(c, dalloc(&c->d_Mq, size_t(P.nelem) * Q3));
+  CK(c, dalloc(&c->d_dinv, n));
+  if (c->colloc) CK(c, dalloc(&c->d_mdiag, n));
+  CK(c, dalloc(&c->d_wl, size_t(nloc) * nc));
+  CK(c, dalloc(&c->d_r, size_t(n) * nc));
+  CK(c, dalloc(&c->d_p, size_t(n) * nc));
+  CK(c, dalloc(&c->d_ax, size_t(n) * nc));
+  CK(c, dalloc(&c->d_state, 1));
+  CK(c, cudaMallocHost(reinterpret_cast<void**>(&c->h_state), sizeof(SolveState)));
+  CK(c, cudaEventCreate(&c->ev0));
+  CK(c, cudaEventCreate(&c->ev1));
+  cudaStream_t s = c->stream;
+  CK(c, cudaMemcpyAsync(c->d_l2g, hl2g.data(), sizeof(int) * nloc, cudaMemcpyHostToDevice, s));
+  CK(c, cudaMemcpyAsync(c->d_off, hoff.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, s));
+  CK(c, cudaMemcpyAsync(c->d_slots, hslots.data(), sizeof(int) * nloc, cudaMemcpyHostToDevice, s));
+  CK(c, cudaMemcpyAsync(c->d_basis, hb.data(), sizeof(double) * hb.size(), cudaMemcpyHostToDevice, s));
+  CK(c, cudaMemsetAsync(c->d_state, 0, sizeof(SolveState), s));
+
+  DeviceMesh& m = c->mesh;
+  m.p1 = p1;
+  m.q = qdef;
+  m.ncomp = nc;
+  m.bp = P.bp;
+  m.colloc = c->colloc;
+  m.nelem = P.nelem;
+  m.nglobal = n;
+  m.l2g = c->d_l2g;
+  m.off = c->d_off;
+  m.slots = c->d_slots;
+  m.basis = c->d_basis;
+
+  const int nb_apply = elem_blocks(m);
+  CK(c, dalloc(&c->d_part_apply, size_t(nb_apply) * nc));
+  CK(c, dalloc(&c->d_part_vec, size_t(vec_blocks(n)) * 3 * nc));
+
+  // ---- geometric and mass factors from the nodal coordinates
+  {
+    double* d_coords = nullptr;
+    double* d_kappa = nullptr;
+    double* d_scratch = nullptr;
+    CK(c, dalloc(&d_coords, size_t(nloc) * 3));
+    CK(c, dalloc(&d_scratch, geom_scratch_doubles(geom_blocks(P.nelem), qdef)));
+    CK(c, cudaMemcpyAsync(d_coords, coords, sizeof(double) * nloc * 3, cudaMemcpyHostToDevice, s));
+    if (kappa && c->op_kind == kStiff) {
+      CK(c, dalloc(&d_kappa, size_t(P.nelem) * Q3));
+      CK(c, cudaMemcpyAsync(d_kappa, kappa, sizeof(double) * P.nelem * Q3, cudaMemcpyHostToDevice, s));
+    }
+    cudaError_t e = launch_geom(m, d_coords, d_kappa, c->d_G, c->d_Mq, d_scratch, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d_coords);
+    cudaFree(d_scratch);
+    if (d_kappa) cudaFree(d_kappa);
+    if (e != cudaSuccess) return cuda_fail(c, e, "geometric factors");
+  }
+  // ---- Jacobi diagonal: local diag(A^e) (or diag(B^e)), summed by Q^T, inverted
+  CK(c, launch_local_diag(m, c->op_kind, c->d_G, c->d_Mq, c->d_wl, s));
+  if (nc == 3) {
+    // the local diagonal is per scalar node; sum it with the scalar layout
+    DeviceMesh m1 = m;
+    m1.ncomp = 1;
+    CK(c, launch_gs(m1, c->d_wl, c->d_r, 0, s));
+  } else {
+    CK(c, launch_gs(m, c->d_wl, c->d_r, 0, s));
+  }
+  CK(c, launch_dinv(c->d_off, c->d_r, c->d_dinv, n, s));
+  if (c->colloc) {
+    DeviceMesh m1 = m;
+    m1.ncomp = 1;
+    CK(c, launch_local_diag(m1, kMass, nullptr, c->d_Mq, c->d_wl, s));
+    CK(c, launch_gs(m1, c->d_wl, c->d_mdiag, 0, s));
+  }
+  // One launch of every element kernel this context uses, so that their
+  // one-time attribute setup happens here and never inside a graph capture.
+  {
+    ElemArgs a{};
+    a.u = c->d_r;
+    a.wl = c->d_wl;
+    a.G = c->op_kind == kStiff ? c->d_G : c->d_Mq;
+    a.mask_in = 1;
+    CK(c, launch_elem(m, c->op_kind, a, s));
+    if (!c->colloc && c->op_kind == kStiff) {
+      a.G = c->d_Mq;
+      CK(c, launch_elem(m, kMass, a, s));
+    }
+  }
+  CK(c, cudaStreamSynchronize(s));
+  return CEEDBP_OK;
+}
+
+void run_iterations(ceedbp_ctx* c, double* x, int n) {
+  const DeviceMesh& m = c->mesh;
+  ElemArgs a{};
+  a.u = c->d_p;
+  a.wl = c->d_wl;
+  a.G = c->op_kind == kStiff ? c->d_G : c->d_Mq;
+  a.partials = c->d_part_apply;
+  a.state = c->d_state;
+  a.mask_in = 0;  // p is zero on Dirichlet nodes
+  a.skip_dirichlet_out = 1;
+  for (int i = 0; i < n; ++i) {
+    launch_elem(m, c->op_kind, a, c->stream);
+    launch_pcg_update(m, c->d_wl, x, c->d_r, c->d_p, c->d_dinv, c->d_part_vec, c->d_state, c->stream);
+    launch_pcg_dir(m, c->d_r, c->d_p, c->d_dinv, c->d_state, c->stream);
+  }
+}
+
+ceedbp_status graph_for(ceedbp_ctx* c, double* x, int n, cudaGraphExec_t* out) {
+  for (auto& g : c->graphs)
+    if (g.x == x && g.n == n) {
+      *out = g.exec;
+      return CEEDBP_OK;
+    }
+  cudaGraph_t graph = nullptr;
+  CK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  run_iterations(c, x, n);
+  cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
+  if (c->graphs.size() >= 8) {
+    cudaGraphExecDestroy(c->graphs.front().exec);
+    c->graphs.erase(c->graphs.begin());
+  }
+  c->graphs.push_back({x, n, exec});
+  *out = exec;
+  return CEEDBP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ceedbp_status ceedbp_setup(const ceedbp_params* params, const double* coords, const int64_t* l2g,
+                           const uint8_t* dirichlet, const double* kappa, void* stream, ceedbp_ctx** out) {
+  if (!params || !out) return fail(nullptr, CEEDBP_EINVAL, "params and out are required");
+  *out = nullptr;
+  ceedbp_ctx* c = new (std::nothrow) ceedbp_ctx();
+  if (!c) return fail(nullptr, CEEDBP_ENOMEM, "host allocation failed");
+  c->prm = *params;
+  c->stream = static_cast<cudaStream_t>(stream);
+  ceedbp_status st = setup_impl(c, coords, l2g, dirichlet, kappa);
+  if (st != CEEDBP_OK) {
+    g_setup_error = c->err;
+    release(c);
+    delete c;
+    return st;
+  }
+  *out = c;
+  return CEEDBP_OK;
+}
+
+ceedbp_status ceedbp_apply(ceedbp_ctx* c, const double* u, double* w) {
+  if (!c || !u || !w) return fail(c, CEEDBP_EINVAL, "null argument");
+  ElemArgs a{};
+  a.u = u;
+  a.wl = c->d_wl;
+  a.G = c->op_kind == kStiff ? c->d_G : c->d_Mq;
+  a.mask_in = c->prm.bp != 1;
+  a.skip_dirichlet_out = 1;
+  CK(c, launch_elem(c->mesh, c->op_kind, a, c->stream));
+  CK(c, launch_gs(c->mesh, c->d_wl, w, 1, c->stream));
+  return CEEDBP_OK;
+}
+
+ceedbp_status ceedbp_mass(ceedbp_ctx* c, const double* u, double* w) {
+  if (!c || !u || !w) return fail(c, CEEDBP_EINVAL, "null argument");
+  if (c->colloc) {
+    CK(c, launch_scale(c->d_mdiag, u, w, c->prm.nglobal, c->ncomp, c->stream));
+    return CEEDBP_OK;
+  }
+  ElemArgs a{};
+  a.u = u;
+  a.wl = c->d_wl;
+  a.G = c->d_Mq;
+  a.mask_in = 0;
+  a.skip_dirichlet_out = 0;
+  CK(c, launch_elem(c->mesh, kMass, a, c->stream));
+  CK(c, launch_gs(c->mesh, c->d_wl, w, 0, c->stream));
+  return CEEDBP_OK;
+}
+
+ceedbp_status ceedbp_jacobi(ceedbp_ctx* c, double* dinv) {
+  if (!c || !dinv) return fail(c, CEEDBP_EINVAL, "null argument");
+  CK(c, cudaMemcpyAsync(dinv, c->d_dinv, sizeof(double) * c->prm.nglobal, cudaMemcpyDeviceToDevice, c->stream));
+  return CEEDBP_OK;
+}
+
+ceedbp_status ceedbp_solve(ceedbp_ctx* c, const double* b, double* x, const ceedbp_solve_opts* opts,
+                           ceedbp_solve_info* info) {
+  if (!c || !b || !x) return fail(c, CEEDBP_EINVAL, "null argument");
+  ceedbp_solve_opts o{1e-8, 10000, 0, 32, 1, 0};
+  if (opts) o = *opts;
+  if (o.chunk <= 0) o.chunk = 32;
+  if (o.maxit <= 0) o.maxit = 10000;
+  if (!(o.tol >= 0.0)) return fail(c, CEEDBP_EINVAL, "tol must be >= 0");
+  const int nc = c->ncomp;
+  const int64_t n = c->prm.nglobal;
+  cudaStream_t s = c->stream;
+  const double* ax = nullptr;
+  if (o.x0_nonzero) {
+    ceedbp_status st = ceedbp_apply(c, x, c->d_ax);
+    if (st != CEEDBP_OK) return st;
+    ax = c->d_ax;
+  } else {
+    CK(c, cudaMemsetAsync(x, 0, sizeof(double) * n * nc, s));
+  }
+  const int fixed = o.fixed_iters > 0 ? 1 : 0;
+  CK(c, launch_pcg_init(c->mesh, b, ax, x, c->d_r, c->d_p, c->d_dinv, c->d_part_vec, c->d_state, o.tol, fixed, s));
+  const int limit = fixed ? o.fixed_iters : o.maxit;
+  const bool graphs = o.use_graph && s != nullptr;
+  CK(c, cudaEventRecord(c->ev0, s));
+  int done = 0;
+  while (done < limit) {
+    const int k = std::min(o.chunk, limit - done);
+    if (graphs) {
+      cudaGraphExec_t exec = nullptr;
+      ceedbp_status st = graph_for(c, x, k, &exec);
+      if (st != CEEDBP_OK) return st;
+      CK(c, cudaGraphLaunch(exec, s));
+    } else {
+      run_iterations(c, x, k);
+      CK(c, cudaGetLastError());
+    }
+    CK(c, cudaEventRecord(c->ev1, s));
+    CK(c, cudaMemcpyAsync(c->h_state, c->d_state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+    CK(c, cudaStreamSynchronize(s));
+    done += k;
+    if (c->h_state->stop) break;
+  }
+  float ms = 0.0f;
+  CK(c, cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+  ceedbp_status result = CEEDBP_OK;
+  const SolveState& h = *c->h_state;
+  for (int comp = 0; comp < nc; ++comp) {
+    if (h.c[comp].status == CEEDBP_EBREAKDOWN) result = CEEDBP_EBREAKDOWN;
+    else if (!fixed && h.c[comp].active && result == CEEDBP_OK) result = CEEDBP_ENOCONV;
+  }
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    for (int comp = 0; comp < nc; ++comp) {
+      const CompScalars& cs = h.c[comp];
+      info->iters[comp] = cs.iters;
+      info->res_norm[comp] = std::sqrt(std::max(cs.rr, 0.0));
+      info->b_norm[comp] = std::sqrt(std::max(cs.bb, 0.0));
+      info->rel_res[comp] = cs.bb > 0.0 ? info->res_norm[comp] / info->b_norm[comp] : 0.0;
+    }
+    info->device_ms = ms;
+    info->status = result;
+  }
+  if (result == CEEDBP_EBREAKDOWN) c->err = "CG breakdown (p^T A p <= 0 or non-finite scalar)";
+  if (result == CEEDBP_ENOCONV) c->err = "maxit reached before the tolerance";
+  return result;
+}
+
+ceedbp_status ceedbp_destroy(ceedbp_ctx* c) {
+  if (!c) return CEEDBP_OK;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  release(c);
+  delete c;
+  return CEEDBP_OK;
+}
+
+const char* ceedbp_last_error(const ceedbp_ctx* c) { return c ? c->err.c_str() : g_setup_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,113 @@
+// Internal declarations shared by the ceedbp translation units (host side).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/ceedbp.h"
+
+namespace ceedbp {
+
+constexpr int kMaxOrder = 15;
+constexpr int kMaxP1 = kMaxOrder + 1;
+constexpr int kMaxQ = kMaxOrder + 2;
+
+// Operator kinds of the element kernel.
+enum OpKind : int { kMass = 0, kStiff = 1 };
+
+// 1D tables of one (order, quadrature) pair, computed on the host (setup).
+struct Basis1D {
+  int p1 = 0, q = 0;
+  bool colloc = false;          // quadrature points are the GLL nodes (BP5/BP6)
+  std::vector<double> xi, rho;  // GLL nodes and weights, p1 each
+  std::vector<double> eta, w;   // quadrature points and weights, q each
+  std::vector<double> J;        // [q][p1] interpolation h_j(eta_q) (identity when colloc)
+  std::vector<double> Dh;       // [q][p1] derivative h_j'(eta_q)
+  std::vector<double> Dq;       // [q][q] derivative of the Lagrange basis on the quadrature points
+};
+
+// Device table layout (doubles): J [q*p1] | Dh [q*p1] | Dq [q*q] | w [q]
+inline size_t basis_doubles(int p1, int q) { return size_t(2) * q * p1 + size_t(q) * q + q; }
+
+bool build_basis(int order, int q, bool gll_quad, Basis1D* out, std::string* err);
+
+// Per-component CG scalars kept on the device.
+struct CompScalars {
+  double rz;     // (r, z) of the current residual
+  double pAp;    // (p, A p)
+  double rr;     // (r, r)
+  double bb;     // (b, b)
+  double alpha, beta;
+  double tol2;   // tol^2 (b, b)
+  int iters;     // iterations performed
+  int active;    // 1 while the component is iterating
+  int status;    // CEEDBP_OK or CEEDBP_EBREAKDOWN
+  int pad;
+};
+
+struct SolveState {
+  CompScalars c[3];
+  int ncomp;
+  int fixed;     // 1: fixed iteration count, never deactivate on tolerance
+  int stop;      // 1: every component inactive; kernels return at once
+  int pad;
+  unsigned int ticket[4];  // last-block counters, one per reduction site
+};
+
+enum TicketSite { kTicketApply = 0, kTicketUpdate = 1, kTicketInit = 2 };
+
+struct DeviceMesh {
+  int p1, q, ncomp, bp;
+  bool colloc;
+  int64_t nelem, nglobal;
+  const int* l2g;       // [E][p1^3]; Dirichlet nodes encoded as -(g+1)
+  const int* off;       // [nglobal+1]; bit 31 of off[g] = Dirichlet flag of node g
+  const int* slots;     // [E p1^3] local slots sorted by node, then slot
+  const double* basis;  // device 1D tables (layout above)
+};
+
+// ---- kernel launchers (one translation unit per family) ----------------------
+// Geometric factors G[e][6][q^3] (kappa-scaled), mass factors M[e][q^3].
+// scratch: at least geom_scratch_doubles(blocks, q) doubles.
+size_t geom_scratch_doubles(int blocks, int q);
+int geom_blocks(int64_t nelem);
+cudaError_t launch_geom(const DeviceMesh& m, const double* coords, const double* kappa,
+                        double* G, double* Mq, double* scratch, cudaStream_t s);
+
+// Local Jacobi contributions diag(A^e) (stiffness) or diag(B^e) (mass) -> wl[E][p1^3]
+cudaError_t launch_local_diag(const DeviceMesh& m, int kind, const double* G, const double* Mq,
+                              double* wl, cudaStream_t s);
+
+// Element operator: wl = A_L (Q u) or B_L (Q u) for ncomp components, optional
+// per-block dot partials of (Q u, wl); mask_in = read Dirichlet nodes as zero.
+struct ElemArgs {
+  const double* u;       // global input [nglobal][ncomp]
+  double* wl;            // local output [E p1^3][ncomp]
+  const double* G;       // stiffness factors or mass factors
+  double* partials;      // [ncomp][nblocks] or nullptr
+  SolveState* state;     // for the fused last-block reduction (alpha) or nullptr
+  int mask_in;
+  int skip_dirichlet_out;
+};
+int elem_blocks(const DeviceMesh& m);
+cudaError_t launch_elem(const DeviceMesh& m, int kind, const ElemArgs& a, cudaStream_t s);
+
+// Gather-scatter sum w[g] = sum_slots wl (masked on Dirichlet nodes if mask_out).
+cudaError_t launch_gs(const DeviceMesh& m, const double* wl, double* w, int mask_out, cudaStream_t s);
+cudaError_t launch_scale(const double* d, const double* u, double* w, int64_t n, int ncomp, cudaStream_t s);
+cudaError_t launch_dinv(const int* off, const double* diag, double* dinv, int64_t n, cudaStream_t s);
+
+// PCG kernels.
+int vec_blocks(int64_t n);
+cudaError_t launch_pcg_init(const DeviceMesh& m, const double* b, const double* ax, double* x, double* r, double* p,
+                            const double* dinv, double* partials, SolveState* st, double tol,
+                            int fixed, cudaStream_t s);
+cudaError_t launch_pcg_update(const DeviceMesh& m, const double* wl, double* x, double* r, const double* p,
+                              const double* dinv, double* partials, SolveState* st, cudaStream_t s);
+cudaError_t launch_pcg_dir(const DeviceMesh& m, const double* r, double* p, const double* dinv,
+                           const SolveState* st, cudaStream_t s);
+
+}  // namespace ceedbp
