@@ -1,0 +1,377 @@
+#!/usr/bin/env python
+"""BP5 Jacobi-PCG throughput on one GB300: DOFs/s per CG iteration, n_0.8, roofline fraction.
+
+The metric is the paper's rate of work (Eq. (3)): DOFs x CG iterations / seconds
+with DOFs = E N^3 (Sec. 2), on a synthetic deformed-box mesh (Sec. 3), BP5
+(Table 1) at order N = 7.  A "step" is one PCG iteration over the whole
+problem: the element kernel (BK5 with the fused p^T A p), the gather-scatter
+plus vector update, and the direction update.  Setup (mesh, geometric factors,
+Jacobi diagonal) is outside the timed region, as in the paper (Sec. 3).
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank solves its own independent problem (replicas,
+weak scaling); rank 0 prints one JSON line.  ``--impl reference`` times the
+CPU FP64 oracle on the host cores instead (a bounded sample of the workload).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BP5 DOFs/sec per CG iter vs n on 1 GB300; n_0.8; % of HBM roofline"
+UNIT = "DOFs/s"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100, help="timed PCG iterations")
+    ap.add_argument("--warmup", type=int, default=5, help="untimed PCG iterations before the timed ones")
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--order", type=int, default=7)
+    ap.add_argument("--k", type=int, default=18, help="E = 2^k elements (N=7: k=18 is n = 8.99e7)")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the n sweep (r_max, n_0.8, t_0.8)")
+    ap.add_argument("--sweep-iters", type=int, default=100)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-k", type=int, default=9, help="E = 2^k elements for the oracle sample")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------------------------------------
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def fp64_peak_tflops(peaks):
+    """FP64 FMA peak of the GB300 derived from its unit count and clock: the nominal
+    1.25 TFLOP/s over 152 SMs at 2070 MHz is 4 flops (2 DFMA) per clock per SM."""
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    return 4.0 * 152 * mhz * 1e6 / 1e12, "derived: 2 DFMA/clk/SM x 152 SMs x sm_max_mhz"
+
+
+def ncu_traffic(name: str):
+    """dram bytes per launch of a kernel from a committed ncu summary (profiles/<name>.md), else None."""
+    path = os.path.join(ROOT, "profiles", name)
+    try:
+        for line in open(path):
+            if line.startswith("dram_bytes_per_launch:"):
+                return float(line.split(":")[1])
+    except OSError:
+        pass
+    return None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: str):
+        self.index = index
+        self.proc = None
+        self.tmp = None
+
+    def start(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.index, f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.tmp, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.2)
+        self.proc.terminate()
+        self.proc.wait(timeout=5)
+        self.tmp.flush()
+        rows = []
+        with open(self.tmp.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 8:
+                    rows.append(parts)
+        os.unlink(self.tmp.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        smax = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------------------------------------
+def bp5_units(N: int):
+    """Algorithmic bytes and flops per DOF (n = E N^3) of the BK5 element kernel and of one PCG
+    iteration (FP64 words): p read once, w written once, six G words per quadrature point,
+    one int32 l2g entry per local node; apply flops 12 p1^4 + 15 p1^3 per element."""
+    p1 = N + 1
+    ratio = (p1 / N) ** 3
+    elem_bytes = 8 * 2 + (6 * 8 + 4) * ratio
+    iter_bytes = 8 * 13 + (6 * 8 + 4) * ratio
+    elem_flops = (12 * p1 ** 4 + 15 * p1 ** 3) / N ** 3
+    return elem_bytes, iter_bytes, elem_flops
+
+
+def n_08(ns, rates):
+    """Smallest n with rate >= 0.8 r_max, log-linearly interpolated between samples."""
+    rmax = max(rates)
+    target = 0.8 * rmax
+    for i, (n, r) in enumerate(zip(ns, rates)):
+        if r >= target:
+            if i == 0:
+                return float(n)
+            n0, r0 = ns[i - 1], rates[i - 1]
+            t = (target - r0) / (r - r0)
+            return float(math.exp(math.log(n0) + t * (math.log(n) - math.log(n0))))
+    return float(ns[-1])
+
+
+def make_problem(pkg, N, k, seed, device):
+    import numpy as np
+    import torch
+
+    from synth import box_dims, uniform_pm1
+    dims = box_dims(k)
+    coords, l2g, dirichlet = pkg.mesh_box(*dims, N, 0.05)
+    op = pkg.Operator(5, N, coords, l2g, dirichlet, device=device)
+    del coords, l2g
+    r = torch.from_numpy(uniform_pm1(seed, np.arange(op.nglobal))).to(device)
+    mask = torch.from_numpy(1.0 - dirichlet.astype(np.float64)).to(device)
+    b = op.mass(r) * mask
+    E = dims[0] * dims[1] * dims[2]
+    return op, b, E * N ** 3, dims
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2004_06722_gb300 as pkg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    N, K, W = args.order, args.steps, max(3, args.warmup)
+
+    op, b, n_dofs, dims = make_problem(pkg, N, args.k, seed=rank, device=device)
+    x = op.empty()
+    # warm-up: graph capture for the timed chunk length, plus W iterations
+    op.solve(b, x, fixed_iters=K, chunk=K)
+    op.solve(b, x, fixed_iters=W, chunk=W)
+    torch.cuda.synchronize()
+
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    clocks = Clocks(vis.split(",")[local] if vis else str(local))
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t0 = time.perf_counter()
+    _, info = op.solve(b, x, fixed_iters=K, chunk=K)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    ms = info["device_ms"]
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * n_dofs * K / (ms * 1e-3)
+
+    # per-kernel durations: the same K-iteration graph with event-record nodes around each kernel
+    _, pinfo = op.solve(b, x, fixed_iters=K, chunk=K, profile=True)
+    elem_ms = pinfo["kernel_ms"][0]
+
+    # end to end through the public API: pinned host RHS in, solution back to pinned host memory
+    b_h = b.cpu().pin_memory()
+    x_h = torch.empty_like(b_h).pin_memory()
+    b_d = torch.empty_like(b)
+    s = torch.cuda.current_stream(device)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(s)
+    b_d.copy_(b_h, non_blocking=True)
+    xe, _ = op.solve(b_d, x, fixed_iters=K, chunk=K)
+    x_h.copy_(xe, non_blocking=True)
+    ev1.record(s)
+    torch.cuda.synchronize()
+    e2e_ms = ev0.elapsed_time(ev1)
+
+    peaks, peak_src = load_peaks()
+    elem_bytes_dof, iter_bytes_dof, elem_flops_dof = bp5_units(N)
+    fp64_tf, fp64_src = fp64_peak_tflops(peaks)
+    elem_flops = elem_flops_dof * n_dofs
+    elem_bytes = elem_bytes_dof * n_dofs
+    t_flop = elem_flops / (fp64_tf * 1e12)
+    t_byte = elem_bytes / (peaks["hbm_gbs"] * 1e9)
+    traffic = ncu_traffic(f"bk5_fp64_n{N}.md")
+    if t_flop >= t_byte:
+        ach = elem_flops / (elem_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": fp64_tf, "unit": "TFLOP/s", "frac": ach / fp64_tf,
+                "traffic": traffic, "kernel": "elem_kernel (BK5, FP64)", "peak_source": fp64_src,
+                "hbm_frac": (elem_bytes / (elem_ms * 1e-3) / 1e9) / peaks["hbm_gbs"]}
+    else:
+        ach = elem_bytes / (elem_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / peaks["hbm_gbs"], "traffic": traffic, "kernel": "elem_kernel (BK5, FP64)",
+                "peak_source": f"{peak_src} hbm_gbs"}
+    roof.update({"elem_ms": elem_ms, "update_ms": pinfo["kernel_ms"][1], "dir_ms": pinfo["kernel_ms"][2],
+                 "algorithmic_bytes_per_dof": elem_bytes_dof, "flops_per_dof": elem_flops_dof})
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"BP5 FP64 Jacobi-PCG, N={N}, E={dims[0]}x{dims[1]}x{dims[2]}={dims[0]*dims[1]*dims[2]} "
+                               f"deformed box (amp 0.05), n=E*N^3={n_dofs}, RHS B*r with r seeded U[-1,1]",
+                   "n": n_dofs, "order": N, "elements": list(dims), "nglobal": op.nglobal,
+                   "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 "
+                   f"(geometric factors {6 * 8 * (N + 1) ** 3 * dims[0] * dims[1] * dims[2] / 1e9:.1f} GB per iteration)",
+                   "timing": "CUDA events around one captured graph of K iterations on the solver stream"},
+        "hbm_roofline": {"bytes_per_dof_iter": iter_bytes_dof,
+                         "roofline_dofs_per_s": peaks["hbm_gbs"] * 1e9 / iter_bytes_dof,
+                         "frac": value / world / (peaks["hbm_gbs"] * 1e9 / iter_bytes_dof)},
+        "roofline": roof,
+        "e2e": {"value": world * n_dofs * K / (e2e_ms * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": b.numel() * 8 / K, "d2h_bytes_per_step": b.numel() * 8 / K,
+                "note": "per solve call of K iterations: H2D of b, solve, D2H of x"},
+        "gpu_launches": 3 * K,
+        "clocks": clk,
+        "wall_s_timed": wall,
+        "solver": {"rel_res_after_K": info["rel_res"][0], "status": info["status"]},
+    }
+    op.close()
+    del b, x
+
+    if not args.no_sweep and rank == 0:
+        line["sweep"] = run_sweep(pkg, N, args.sweep_iters, device)
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        line["cpu_baseline"] = cpu_baseline(N, args.cpu_sample_k, iters=20)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_sweep(pkg, N, iters, device):
+    import torch
+
+    from synth import sweep_ks
+    ns, rates, times = [], [], []
+    for k in sweep_ks(N):
+        op, b, n_dofs, dims = make_problem(pkg, N, k, seed=0, device=device)
+        x = op.empty()
+        op.solve(b, x, fixed_iters=iters, chunk=iters)
+        best = None
+        for _ in range(3):
+            _, info = op.solve(b, x, fixed_iters=iters, chunk=iters)
+            best = info["device_ms"] if best is None else min(best, info["device_ms"])
+        ns.append(n_dofs)
+        rates.append(n_dofs * iters / (best * 1e-3))
+        times.append(best / iters)
+        op.close()
+        del b, x
+        torch.cuda.empty_cache()
+    rmax = max(rates)
+    n80 = n_08(ns, rates)
+    return {"order": N, "iters": iters, "n": ns, "dofs_per_s": rates, "s_per_iter": times,
+            "r_max": rmax, "n_0.8": n80, "t_0.8": 1.25 * n80 / rmax}
+
+
+def cpu_baseline(N, k, iters):
+    """The oracle as it stands (assembled CSR, textbook PCG) on a bounded sample: BP5 at the same
+    order on E = 2^k elements; rate = E N^3 x iterations / PCG seconds (assembly excluded)."""
+    import numpy as np
+
+    from oracle.problems import BakeoffProblem
+    from synth import box_dims, uniform_pm1
+    dims = box_dims(k)
+    t0 = time.perf_counter()
+    prob = BakeoffProblem(5, *dims, N, amp=0.05)
+    t_setup = time.perf_counter() - t0
+    b = prob.rhs(uniform_pm1(0, np.arange(prob.n_global)))
+    t0 = time.perf_counter()
+    prob.solve(b, fixed_iters=iters)
+    t = time.perf_counter() - t0
+    n = dims[0] * dims[1] * dims[2] * N ** 3
+    return {"value": n * iters / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"BP5 N={N}, E={dims[0]}x{dims[1]}x{dims[2]} (n={n}), {iters} PCG iterations on the "
+                      f"assembled CSR matrix (scipy SpMV, one thread); assembly {t_setup:.1f} s excluded",
+            "host_cpus": os.cpu_count()}
+
+
+def run_reference(args):
+    """The oracle timed on the host cores, one PCG iteration per step, on a bounded sample."""
+    import numpy as np
+
+    from oracle.pcg import pcg
+    from oracle.problems import BakeoffProblem
+    from synth import box_dims, uniform_pm1
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    N, K, W = args.order, args.steps, max(3, args.warmup)
+    dims = box_dims(args.cpu_sample_k)
+    prob = BakeoffProblem(5, *dims, N, amp=0.05)
+    b = prob.rhs(uniform_pm1(0, np.arange(prob.n_global)))[prob.free]
+    pcg(prob.A_free, b, prob.diag_free, fixed_iters=W)
+    t0 = time.perf_counter()
+    pcg(prob.A_free, b, prob.diag_free, fixed_iters=K)
+    t = time.perf_counter() - t0
+    n = dims[0] * dims[1] * dims[2] * N ** 3
+    big = box_dims(args.k)
+    value = n * K / t
+    sample = (f"BP5 N={N}, E={dims[0]}x{dims[1]}x{dims[2]} (n={n}) instead of E=2^{args.k}; "
+              f"{K} PCG iterations of the oracle (assembled CSR, scipy SpMV, one thread)")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": K, "warmup": W, "ms_per_step": t / K * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"BP5 FP64 Jacobi-PCG, N={N}, E={big[0]}x{big[1]}x{big[2]} deformed box",
+                   "order": N},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

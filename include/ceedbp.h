@@ -136,6 +136,8 @@ typedef struct {
   int chunk;         /* iterations per launched CUDA graph between host checks; 0 = 32 */
   int use_graph;     /* 1 = capture chunks in CUDA graphs (default), 0 = plain launches */
   int x0_nonzero;    /* 1 = x_dev holds an initial guess; 0 = start from x = 0 */
+  int profile;       /* 1 = record CUDA events around every kernel (inside the graph) and
+                        report per-kernel mean durations in info->kernel_ms */
 } ceedbp_solve_opts;
 
 typedef struct {
@@ -144,6 +146,8 @@ typedef struct {
   double res_norm[3];
   double b_norm[3];
   double device_ms;  /* time of the iteration loop measured with CUDA events */
+  double kernel_ms[3]; /* with opts->profile: mean duration of the element, update and
+                          direction kernels over the iterations run (0 otherwise) */
   int status;        /* same as the return value */
 } ceedbp_solve_info;
 

@@ -34,18 +34,20 @@ class Params(ctypes.Structure):
 
 class SolveOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("maxit", ctypes.c_int), ("fixed_iters", ctypes.c_int),
-                ("chunk", ctypes.c_int), ("use_graph", ctypes.c_int), ("x0_nonzero", ctypes.c_int)]
+                ("chunk", ctypes.c_int), ("use_graph", ctypes.c_int), ("x0_nonzero", ctypes.c_int),
+                ("profile", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int * 3), ("rel_res", ctypes.c_double * 3),
                 ("res_norm", ctypes.c_double * 3), ("b_norm", ctypes.c_double * 3),
-                ("device_ms", ctypes.c_double), ("status", ctypes.c_int)]
+                ("device_ms", ctypes.c_double), ("kernel_ms", ctypes.c_double * 3), ("status", ctypes.c_int)]
 
     def as_dict(self, ncomp: int) -> dict:
         return {"iters": list(self.iters[:ncomp]), "rel_res": list(self.rel_res[:ncomp]),
                 "res_norm": list(self.res_norm[:ncomp]), "b_norm": list(self.b_norm[:ncomp]),
-                "device_ms": self.device_ms, "status": STATUS_NAMES.get(self.status, self.status)}
+                "device_ms": self.device_ms, "kernel_ms": list(self.kernel_ms),
+                "status": STATUS_NAMES.get(self.status, self.status)}
 
 
 _P = ctypes.c_void_p
@@ -190,9 +192,9 @@ class Operator:
         return d
 
     def solve(self, b, x=None, tol: float = 1e-8, maxit: int = 10000, fixed_iters: int = 0, chunk: int = 32,
-              use_graph: bool = True, x0=False, raise_on_noconv: bool = True):
+              use_graph: bool = True, x0=False, raise_on_noconv: bool = True, profile: bool = False):
         x = self.empty() if x is None else x
-        opts = SolveOpts(tol, maxit, fixed_iters, chunk, int(use_graph), int(bool(x0)))
+        opts = SolveOpts(tol, maxit, fixed_iters, chunk, int(use_graph), int(bool(x0)), int(profile))
         info = SolveInfo()
         st = self._call(self.lib.ceedbp_solve, self._vec(b), self._vec(x), ctypes.byref(opts), ctypes.byref(info))
         if st != OK and (raise_on_noconv or st != ENOCONV):

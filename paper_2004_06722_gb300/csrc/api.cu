@@ -39,6 +39,7 @@ using namespace ceedbp;
 struct GraphEntry {
   double* x;
   int n;
+  int profile;
   cudaGraphExec_t exec;
 };
 
@@ -65,6 +66,7 @@ struct ceedbp_ctx {
   SolveState* d_state = nullptr;
   SolveState* h_state = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::vector<cudaEvent_t> prof;  // 4 events per profiled iteration
   std::vector<GraphEntry> graphs;
   std::string err;
 };
@@ -105,6 +107,8 @@ void release(ceedbp_ctx* c) {
   if (c->h_state) cudaFreeHost(c->h_state);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
+  for (cudaEvent_t e : c->prof) cudaEventDestroy(e);
+  c->prof.clear();
 }
 
 ceedbp_status setup_impl(ceedbp_ctx* c, const double* coords, const int64_t* l2g, const uint8_t* dirichlet,
@@ -252,7 +256,13 @@ ceedbp_status setup_impl(ceedbp_ctx* c, const double* coords, const int64_t* l2g
   return CEEDBP_OK;
 }
 
-void run_iterations(ceedbp_ctx* c, double* x, int n) {
+// Events recorded inside a capture become event-record nodes of the graph.
+void mark(ceedbp_ctx* c, int i, bool capturing) {
+  if (capturing) cudaEventRecordWithFlags(c->prof[i], c->stream, cudaEventRecordExternal);
+  else cudaEventRecord(c->prof[i], c->stream);
+}
+
+void run_iterations(ceedbp_ctx* c, double* x, int n, bool profile = false, bool capturing = false) {
   const DeviceMesh& m = c->mesh;
   ElemArgs a{};
   a.u = c->d_p;
@@ -263,21 +273,34 @@ void run_iterations(ceedbp_ctx* c, double* x, int n) {
   a.mask_in = 0;  // p is zero on Dirichlet nodes
   a.skip_dirichlet_out = 1;
   for (int i = 0; i < n; ++i) {
+    if (profile) mark(c, 4 * i + 0, capturing);
     launch_elem(m, c->op_kind, a, c->stream);
+    if (profile) mark(c, 4 * i + 1, capturing);
     launch_pcg_update(m, c->d_wl, x, c->d_r, c->d_p, c->d_dinv, c->d_part_vec, c->d_state, c->stream);
+    if (profile) mark(c, 4 * i + 2, capturing);
     launch_pcg_dir(m, c->d_r, c->d_p, c->d_dinv, c->d_state, c->stream);
+    if (profile) mark(c, 4 * i + 3, capturing);
   }
 }
 
-ceedbp_status graph_for(ceedbp_ctx* c, double* x, int n, cudaGraphExec_t* out) {
+ceedbp_status ensure_prof_events(ceedbp_ctx* c, int n) {
+  while (int(c->prof.size()) < 4 * n) {
+    cudaEvent_t e = nullptr;
+    CK(c, cudaEventCreate(&e));
+    c->prof.push_back(e);
+  }
+  return CEEDBP_OK;
+}
+
+ceedbp_status graph_for(ceedbp_ctx* c, double* x, int n, int profile, cudaGraphExec_t* out) {
   for (auto& g : c->graphs)
-    if (g.x == x && g.n == n) {
+    if (g.x == x && g.n == n && g.profile == profile) {
       *out = g.exec;
       return CEEDBP_OK;
     }
   cudaGraph_t graph = nullptr;
   CK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-  run_iterations(c, x, n);
+  run_iterations(c, x, n, profile != 0, true);
   cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
   cudaGraphExec_t exec = nullptr;
@@ -288,7 +311,7 @@ ceedbp_status graph_for(ceedbp_ctx* c, double* x, int n, cudaGraphExec_t* out) {
     cudaGraphExecDestroy(c->graphs.front().exec);
     c->graphs.erase(c->graphs.begin());
   }
-  c->graphs.push_back({x, n, exec});
+  c->graphs.push_back({x, n, profile, exec});
   *out = exec;
   return CEEDBP_OK;
 }
@@ -355,7 +378,7 @@ ceedbp_status ceedbp_jacobi(ceedbp_ctx* c, double* dinv) {
 ceedbp_status ceedbp_solve(ceedbp_ctx* c, const double* b, double* x, const ceedbp_solve_opts* opts,
                            ceedbp_solve_info* info) {
   if (!c || !b || !x) return fail(c, CEEDBP_EINVAL, "null argument");
-  ceedbp_solve_opts o{1e-8, 10000, 0, 32, 1, 0};
+  ceedbp_solve_opts o{1e-8, 10000, 0, 32, 1, 0, 0};
   if (opts) o = *opts;
   if (o.chunk <= 0) o.chunk = 32;
   if (o.maxit <= 0) o.maxit = 10000;
@@ -375,22 +398,39 @@ ceedbp_status ceedbp_solve(ceedbp_ctx* c, const double* b, double* x, const ceed
   CK(c, launch_pcg_init(c->mesh, b, ax, x, c->d_r, c->d_p, c->d_dinv, c->d_part_vec, c->d_state, o.tol, fixed, s));
   const int limit = fixed ? o.fixed_iters : o.maxit;
   const bool graphs = o.use_graph && s != nullptr;
+  const bool profile = o.profile != 0;
+  if (profile) {
+    ceedbp_status st = ensure_prof_events(c, std::min(o.chunk, limit));
+    if (st != CEEDBP_OK) return st;
+  }
+  double kms[3] = {0.0, 0.0, 0.0};
+  int kcount = 0;
   CK(c, cudaEventRecord(c->ev0, s));
   int done = 0;
   while (done < limit) {
     const int k = std::min(o.chunk, limit - done);
     if (graphs) {
       cudaGraphExec_t exec = nullptr;
-      ceedbp_status st = graph_for(c, x, k, &exec);
+      ceedbp_status st = graph_for(c, x, k, profile ? 1 : 0, &exec);
       if (st != CEEDBP_OK) return st;
       CK(c, cudaGraphLaunch(exec, s));
     } else {
-      run_iterations(c, x, k);
+      run_iterations(c, x, k, profile, false);
       CK(c, cudaGetLastError());
     }
     CK(c, cudaEventRecord(c->ev1, s));
     CK(c, cudaMemcpyAsync(c->h_state, c->d_state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
     CK(c, cudaStreamSynchronize(s));
+    if (profile) {
+      for (int i = 0; i < k; ++i) {
+        float t = 0.0f;
+        for (int j = 0; j < 3; ++j) {
+          CK(c, cudaEventElapsedTime(&t, c->prof[4 * i + j], c->prof[4 * i + j + 1]));
+          kms[j] += t;
+        }
+      }
+      kcount += k;
+    }
     done += k;
     if (c->h_state->stop) break;
   }
@@ -412,6 +452,7 @@ ceedbp_status ceedbp_solve(ceedbp_ctx* c, const double* b, double* x, const ceed
       info->rel_res[comp] = cs.bb > 0.0 ? info->res_norm[comp] / info->b_norm[comp] : 0.0;
     }
     info->device_ms = ms;
+    for (int j = 0; j < 3; ++j) info->kernel_ms[j] = kcount ? kms[j] / kcount : 0.0;
     info->status = result;
   }
   if (result == CEEDBP_EBREAKDOWN) c->err = "CG breakdown (p^T A p <= 0 or non-finite scalar)";
