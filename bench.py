@@ -288,7 +288,7 @@ def run_sweep(pkg, N, iters, device):
     import torch
 
     from synth import sweep_ks
-    ns, rates, times = [], [], []
+    ns, rates, ms_iter = [], [], []
     for k in sweep_ks(N):
         op, b, n_dofs, dims = make_problem(pkg, N, k, seed=0, device=device)
         x = op.empty()
@@ -299,14 +299,14 @@ def run_sweep(pkg, N, iters, device):
             best = info["device_ms"] if best is None else min(best, info["device_ms"])
         ns.append(n_dofs)
         rates.append(n_dofs * iters / (best * 1e-3))
-        times.append(best / iters)
+        ms_iter.append(best / iters)
         op.close()
         del b, x
         torch.cuda.empty_cache()
     rmax = max(rates)
     n80 = n_08(ns, rates)
-    return {"order": N, "iters": iters, "n": ns, "dofs_per_s": rates, "s_per_iter": times,
-            "r_max": rmax, "n_0.8": n80, "t_0.8": 1.25 * n80 / rmax}
+    return {"order": N, "iters": iters, "n": ns, "dofs_per_s": rates, "ms_per_iter": ms_iter,
+            "r_max": rmax, "n_0.8": n80, "t_0.8_s": 1.25 * n80 / rmax}
 
 
 def cpu_baseline(N, k, iters):
