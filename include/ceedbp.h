@@ -162,6 +162,29 @@ typedef struct {
 ceedbp_status ceedbp_solve(ceedbp_ctx* ctx, const double* b_dev, double* x_dev,
                            const ceedbp_solve_opts* opts, ceedbp_solve_info* info);
 
+/*
+ * ceedbp_apply without any allocation (the paper has no counterpart; this is
+ * a service for callers that cannot call cudaMalloc where they apply the
+ * operator -- e.g. while another thread holds a global-mode stream capture,
+ * when another allocator owns the device memory, or in time-critical loops
+ * that cannot take cudaMalloc's implicit synchronisation).
+ * Computes the same w as ceedbp_apply(ctx, u_dev, w_dev), on `stream`
+ * (cudaStream_t, NULL = legacy default), using for the element-local scratch
+ * a file-scope device array of 32 MiB (2^22 doubles) that every GPU loading
+ * the library holds until the process exits, instead of the context's buffer.
+ *   ctx    a context from ceedbp_setup (read only; its own scratch is untouched)
+ *   u_dev  device FP64 [nglobal][ncomp] input, w_dev device FP64 output.
+ * Limit: E * (N+1)^3 * ncomp <= 2^22 (N = 7: 8192 scalar elements); larger
+ * problems return CEEDBP_EINVAL with a message on stderr and launch nothing.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress with that device current); make that first call
+ * before any stream capture.  All calls share the one array: calls whose
+ * kernels overlap on the GPU (other streams, other threads) race on it.  Each
+ * call writes every scratch entry it later reads, so nothing needs clearing.
+ */
+ceedbp_status ceedbp_apply_noalloc(const ceedbp_ctx* ctx, const double* u_dev, double* w_dev,
+                                   void* stream);
+
 /* Release every resource owned by ctx (NULL is accepted). */
 ceedbp_status ceedbp_destroy(ceedbp_ctx* ctx);
 

@@ -59,6 +59,7 @@ _SIGS = {
     "ceedbp_mass": (ctypes.c_int, [_P, _P, _P]),
     "ceedbp_jacobi": (ctypes.c_int, [_P, _P]),
     "ceedbp_solve": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo)]),
+    "ceedbp_apply_noalloc": (ctypes.c_int, [_P, _P, _P, _P]),
     "ceedbp_destroy": (ctypes.c_int, [_P]),
     "ceedbp_last_error": (ctypes.c_char_p, [_P]),
 }
@@ -178,6 +179,15 @@ class Operator:
     def apply(self, u, out=None):
         w = self.empty() if out is None else out
         _check(self._call(self.lib.ceedbp_apply, self._vec(u), self._vec(w)), self.ctx)
+        return w
+
+    def apply_noalloc(self, u, out=None):
+        """ceedbp_apply_noalloc: same result as apply(), scratch in the library's static
+        device array (no allocation), on this operator's stream."""
+        w = self.empty() if out is None else out
+        st = self._call(lambda ctx, a, b: self.lib.ceedbp_apply_noalloc(ctx, a, b, ctypes.c_void_p(self.stream.cuda_stream)),
+                        self._vec(u), self._vec(w))
+        _check(st, self.ctx)
         return w
 
     def mass(self, u, out=None):
