@@ -54,11 +54,12 @@ typedef enum {
   CEEDBP_EUNSUPPORTED = 6 /* combination of options not built */
 } ceedbp_status;
 
-/* Arithmetic of the operator inside solve/apply. */
+/* Arithmetic of the FP64 operator and solver (ceedbp_params.arith). */
 enum {
-  CEEDBP_FP64 = 0,      /* FP64 storage and arithmetic */
-  CEEDBP_FP32 = 1,      /* inner operator: FP32 storage and arithmetic */
-  CEEDBP_BF16STORE = 2  /* inner operator: BF16 storage of u and G, FP32 arithmetic */
+  CEEDBP_ARITH_FP64 = 0, /* native FP64 instructions */
+  CEEDBP_ARITH_DF64 = 1  /* FP64-accurate pairs of FP32 numbers (hi + lo, ~2^-46 relative per
+                            value) on the FP32 pipe, which the GB300 issues 59x faster than
+                            FP64; BP5 and BP6 only.  Results match the FP64 path to ~1e-14. */
 };
 
 typedef struct {
@@ -67,6 +68,7 @@ typedef struct {
   int nquad;        /* quadrature points per direction; 0 = the BP's rule (N+2 GL or N+1 GLL) */
   int64_t nelem;    /* E, number of hexahedral elements */
   int64_t nglobal;  /* number of unique nodes */
+  int arith;        /* CEEDBP_ARITH_FP64 or CEEDBP_ARITH_DF64 (apply and solve) */
 } ceedbp_params;
 
 /*
@@ -126,6 +128,22 @@ ceedbp_status ceedbp_apply(ceedbp_ctx* ctx, const double* u_dev, double* w_dev);
  */
 ceedbp_status ceedbp_mass(ceedbp_ctx* ctx, const double* u_dev, double* w_dev);
 
+/* Inner precision of FP64 defect correction (ceedbp_prepare_mixed, solve opts.mixed). */
+enum {
+  CEEDBP_MIXED_NONE = 0,
+  CEEDBP_MIXED_FP32 = 1, /* inner operator and vectors in FP32 */
+  CEEDBP_MIXED_BF16 = 2  /* inner G and direction p stored in BF16, FP32 arithmetic */
+};
+
+/*
+ * Prepare defect-correction solves (BP5/BP6): allocates the low-precision copy
+ * of the geometric factors (FP32 or BF16, rounded to nearest from the FP64
+ * factors of Eq. (23)) and the FP32 inner CG vectors.  Call once per
+ * precision before ceedbp_solve with opts->mixed = precision.
+ * Errors: EUNSUPPORTED (BP1/BP3), EINVAL, ENOMEM, ECUDA.
+ */
+ceedbp_status ceedbp_prepare_mixed(ceedbp_ctx* ctx, int precision);
+
 /* Jacobi preconditioner: dinv_dev[nglobal] receives 1/diag (0 on Dirichlet nodes). */
 ceedbp_status ceedbp_jacobi(ceedbp_ctx* ctx, double* dinv_dev);
 
@@ -138,6 +156,12 @@ typedef struct {
   int x0_nonzero;    /* 1 = x_dev holds an initial guess; 0 = start from x = 0 */
   int profile;       /* 1 = record CUDA events around every kernel (inside the graph) and
                         report per-kernel mean durations in info->kernel_ms */
+  int mixed;         /* CEEDBP_MIXED_*: FP64 defect correction around a low-precision inner
+                        PCG (outer residual r = b - A x, update x += d and all CG inner
+                        products in FP64 accuracy); tol applies to the FP64 residual */
+  double inner_tol;  /* inner relative tolerance (0 = 1e-4 for FP32, 3e-3 for BF16) */
+  int inner_maxit;   /* inner iteration limit per outer step (0 = maxit) */
+  int outer_maxit;   /* outer step limit (0 = 50) */
 } ceedbp_solve_opts;
 
 typedef struct {
@@ -149,11 +173,13 @@ typedef struct {
   double kernel_ms[3]; /* with opts->profile: mean duration of the element, update and
                           direction kernels over the iterations run (0 otherwise) */
   int status;        /* same as the return value */
+  int outer_iters;   /* defect-correction steps (0 for plain solves) */
 } ceedbp_solve_info;
 
 /*
  * Jacobi-PCG (Sec. 3) on the assembled system, one independent CG per
- * component (BP6).  b_dev: device [nglobal][ncomp]; x_dev: device
+ * component (BP6); with opts->mixed, FP64 defect correction around a
+ * low-precision inner Jacobi-PCG (info->iters then counts inner iterations).  b_dev: device [nglobal][ncomp]; x_dev: device
  * [nglobal][ncomp], in: initial guess when opts->x0_nonzero, out: solution.
  * All CG scalars stay on the device; each iteration is two fused kernels plus
  * one direction update, launched from a captured CUDA graph.
@@ -184,6 +210,56 @@ ceedbp_status ceedbp_solve(ceedbp_ctx* ctx, const double* b_dev, double* x_dev,
  */
 ceedbp_status ceedbp_apply_noalloc(const ceedbp_ctx* ctx, const double* u_dev, double* w_dev,
                                    void* stream);
+
+/*
+ * Variable coefficient (Eq. (4) with mu = kappa): replace the coefficient at
+ * the quadrature points, kappa_dev device FP64 [E][q^3] (q^3 points of element
+ * e at kappa_dev + e q^3, point index qx + q (qy + q qz)).  The stiffness
+ * factors become kappa Ghat (Ghat: Eq. (23) without coefficient) and the
+ * Jacobi diagonal (and any FP32-pair or low-precision copies) are recomputed.
+ * Stiffness problems only; EUNSUPPORTED for BP1.
+ */
+ceedbp_status ceedbp_set_kappa(ceedbp_ctx* ctx, const double* kappa_dev);
+
+/*
+ * Misfit J = 1/2 (u - u*)^T B (u - u*) with B the BP's mass (diagonal GLL mass,
+ * BP5 only) and the adjoint right-hand side rhs = M B (u - u*).
+ *   u_dev, ustar_dev: device FP64 [nglobal]; rhs_dev: device output [nglobal];
+ *   J: host output (the call synchronises the stream).
+ */
+ceedbp_status ceedbp_misfit(ceedbp_ctx* ctx, const double* u_dev, const double* ustar_dev, double* rhs_dev,
+                            double* J);
+
+/*
+ * Adjoint gradient of J(kappa): g_dev[e][q] = -(grad lambda)_q . Ghat_q (grad u)_q
+ * = dJ/dkappa_{e,q} for the solution u of A(kappa) u = b and the adjoint
+ * lambda of A(kappa) lambda = M B (u - u*) (ceedbp_misfit's rhs; one solve,
+ * A is symmetric).  BP5 (collocated quadrature), orders 1..11.
+ *   u_dev, lambda_dev: device FP64 [nglobal]; g_dev: device FP64 [E][q^3].
+ */
+ceedbp_status ceedbp_kappa_gradient(ceedbp_ctx* ctx, const double* u_dev, const double* lambda_dev, double* g_dev);
+
+/*
+ * Batched BP5 solves: nprob independent problems (own mesh, order, size) set
+ * up together and solved by one batched Jacobi-PCG whose every phase is one
+ * launch per polynomial order for all problems, captured in CUDA graphs.
+ * Arithmetic: FP64-accurate FP32 pairs (CEEDBP_ARITH_DF64); elements per
+ * block per order chosen by the setup autotuner.  Each problem stops at its
+ * own tolerance.
+ *   params[p], coords[p], l2g[p], dirichlet[p]: as for ceedbp_setup (host);
+ *   params[p].bp must be 5.
+ * ceedbp_batch_solve: b_dev[p], x_dev[p] device FP64 [params[p].nglobal]
+ * (host arrays of device pointers); opts->tol, maxit, chunk, use_graph are
+ * used; infos[p] (may be NULL) receives each problem's result.
+ */
+typedef struct ceedbp_batch ceedbp_batch;
+ceedbp_status ceedbp_batch_setup(int nprob, const ceedbp_params* params, const double* const* coords,
+                                 const int64_t* const* l2g, const uint8_t* const* dirichlet, void* stream,
+                                 ceedbp_batch** out);
+ceedbp_status ceedbp_batch_solve(ceedbp_batch* batch, const double* const* b_dev, double* const* x_dev,
+                                 const ceedbp_solve_opts* opts, ceedbp_solve_info* infos);
+ceedbp_status ceedbp_batch_destroy(ceedbp_batch* batch);
+const char* ceedbp_batch_last_error(const ceedbp_batch* batch);
 
 /* Release every resource owned by ctx (NULL is accepted). */
 ceedbp_status ceedbp_destroy(ceedbp_ctx* ctx);

@@ -18,7 +18,8 @@ LIB_PATH = os.path.join(_PKG, "libceedbp.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, EBREAKDOWN, EUNSUPPORTED = range(7)
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "EBREAKDOWN", 6: "EUNSUPPORTED"}
-FP64, FP32, BF16STORE = 0, 1, 2
+ARITH_FP64, ARITH_DF64 = 0, 1
+MIXED_NONE, MIXED_FP32, MIXED_BF16 = 0, 1, 2
 
 
 class CeedbpError(RuntimeError):
@@ -29,25 +30,27 @@ class CeedbpError(RuntimeError):
 
 class Params(ctypes.Structure):
     _fields_ = [("bp", ctypes.c_int), ("order", ctypes.c_int), ("nquad", ctypes.c_int),
-                ("nelem", ctypes.c_int64), ("nglobal", ctypes.c_int64)]
+                ("nelem", ctypes.c_int64), ("nglobal", ctypes.c_int64), ("arith", ctypes.c_int)]
 
 
 class SolveOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("maxit", ctypes.c_int), ("fixed_iters", ctypes.c_int),
                 ("chunk", ctypes.c_int), ("use_graph", ctypes.c_int), ("x0_nonzero", ctypes.c_int),
-                ("profile", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("mixed", ctypes.c_int), ("inner_tol", ctypes.c_double),
+                ("inner_maxit", ctypes.c_int), ("outer_maxit", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int * 3), ("rel_res", ctypes.c_double * 3),
                 ("res_norm", ctypes.c_double * 3), ("b_norm", ctypes.c_double * 3),
-                ("device_ms", ctypes.c_double), ("kernel_ms", ctypes.c_double * 3), ("status", ctypes.c_int)]
+                ("device_ms", ctypes.c_double), ("kernel_ms", ctypes.c_double * 3), ("status", ctypes.c_int),
+                ("outer_iters", ctypes.c_int)]
 
     def as_dict(self, ncomp: int) -> dict:
         return {"iters": list(self.iters[:ncomp]), "rel_res": list(self.rel_res[:ncomp]),
                 "res_norm": list(self.res_norm[:ncomp]), "b_norm": list(self.b_norm[:ncomp]),
                 "device_ms": self.device_ms, "kernel_ms": list(self.kernel_ms),
-                "status": STATUS_NAMES.get(self.status, self.status)}
+                "status": STATUS_NAMES.get(self.status, self.status), "outer_iters": self.outer_iters}
 
 
 _P = ctypes.c_void_p
@@ -58,9 +61,19 @@ _SIGS = {
     "ceedbp_apply": (ctypes.c_int, [_P, _P, _P]),
     "ceedbp_mass": (ctypes.c_int, [_P, _P, _P]),
     "ceedbp_jacobi": (ctypes.c_int, [_P, _P]),
+    "ceedbp_prepare_mixed": (ctypes.c_int, [_P, ctypes.c_int]),
+    "ceedbp_set_kappa": (ctypes.c_int, [_P, _P]),
+    "ceedbp_misfit": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
+    "ceedbp_kappa_gradient": (ctypes.c_int, [_P, _P, _P, _P]),
     "ceedbp_solve": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo)]),
     "ceedbp_apply_noalloc": (ctypes.c_int, [_P, _P, _P, _P]),
     "ceedbp_destroy": (ctypes.c_int, [_P]),
+    "ceedbp_batch_setup": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(Params), ctypes.POINTER(_P),
+                                          ctypes.POINTER(_P), ctypes.POINTER(_P), _P, ctypes.POINTER(_P)]),
+    "ceedbp_batch_solve": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(SolveOpts),
+                                          ctypes.POINTER(SolveInfo)]),
+    "ceedbp_batch_destroy": (ctypes.c_int, [_P]),
+    "ceedbp_batch_last_error": (ctypes.c_char_p, [_P]),
     "ceedbp_last_error": (ctypes.c_char_p, [_P]),
 }
 
@@ -111,7 +124,7 @@ class Operator:
     """One bake-off problem on the GPU: ceedbp_setup / apply / mass / solve / destroy."""
 
     def __init__(self, bp: int, order: int, coords: np.ndarray, l2g: np.ndarray, dirichlet: np.ndarray | None,
-                 kappa: np.ndarray | None = None, stream=None, device=None):
+                 kappa: np.ndarray | None = None, stream=None, device=None, arith: int = 0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("ceedbp needs a CUDA device; there is no CPU path")
@@ -127,7 +140,8 @@ class Operator:
         self.nglobal = int(dirichlet.shape[0]) if dirichlet is not None else int(l2g.max()) + 1
         dirichlet = None if dirichlet is None else np.ascontiguousarray(dirichlet, dtype=np.uint8)
         kappa = None if kappa is None else np.ascontiguousarray(kappa, dtype=np.float64)
-        prm = Params(bp, order, 0, self.nelem, self.nglobal)
+        self.arith = arith
+        prm = Params(bp, order, 0, self.nelem, self.nglobal, arith)
         ctx = ctypes.c_void_p()
         cur = torch.cuda.current_stream(self.device)
         self.stream.wait_stream(cur)
@@ -201,10 +215,47 @@ class Operator:
         _check(self._call(self.lib.ceedbp_jacobi, ctypes.c_void_p(d.data_ptr())), self.ctx)
         return d
 
+    def _ptr_t(self, t, numel=None):
+        import torch
+        if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+            raise ValueError("expected a contiguous float64 CUDA tensor")
+        if numel is not None and t.numel() != numel:
+            raise ValueError(f"tensor has {t.numel()} entries, expected {numel}")
+        return ctypes.c_void_p(t.data_ptr())
+
+    @property
+    def nquad(self) -> int:
+        return self.order + 1 if self.bp in (5, 6) else self.order + 2
+
+    def set_kappa(self, kappa):
+        """kappa: float64 CUDA tensor [E, q^3] at the quadrature points."""
+        _check(self._call(self.lib.ceedbp_set_kappa, self._ptr_t(kappa, self.nelem * self.nquad ** 3)), self.ctx)
+
+    def misfit(self, u, u_star, rhs=None):
+        """J = 1/2 (u - u*)^T B (u - u*) and the adjoint RHS M B (u - u*)."""
+        rhs = self.empty() if rhs is None else rhs
+        J = ctypes.c_double(0.0)
+        _check(self._call(self.lib.ceedbp_misfit, self._vec(u), self._vec(u_star), self._vec(rhs),
+                          ctypes.byref(J)), self.ctx)
+        return rhs, J.value
+
+    def kappa_gradient(self, u, lam, out=None):
+        import torch
+        g = out if out is not None else torch.empty((self.nelem, self.nquad ** 3), dtype=torch.float64,
+                                                     device=self.device)
+        _check(self._call(self.lib.ceedbp_kappa_gradient, self._vec(u), self._vec(lam),
+                          self._ptr_t(g, self.nelem * self.nquad ** 3)), self.ctx)
+        return g
+
+    def prepare_mixed(self, precision: int):
+        _check(self._call(self.lib.ceedbp_prepare_mixed, precision), self.ctx)
+
     def solve(self, b, x=None, tol: float = 1e-8, maxit: int = 10000, fixed_iters: int = 0, chunk: int = 32,
-              use_graph: bool = True, x0=False, raise_on_noconv: bool = True, profile: bool = False):
+              use_graph: bool = True, x0=False, raise_on_noconv: bool = True, profile: bool = False,
+              mixed: int = 0, inner_tol: float = 0.0, inner_maxit: int = 0, outer_maxit: int = 0):
         x = self.empty() if x is None else x
-        opts = SolveOpts(tol, maxit, fixed_iters, chunk, int(use_graph), int(bool(x0)), int(profile))
+        opts = SolveOpts(tol, maxit, fixed_iters, chunk, int(use_graph), int(bool(x0)), int(profile),
+                         int(mixed), float(inner_tol), int(inner_maxit), int(outer_maxit))
         info = SolveInfo()
         st = self._call(self.lib.ceedbp_solve, self._vec(b), self._vec(x), ctypes.byref(opts), ctypes.byref(info))
         if st != OK and (raise_on_noconv or st != ENOCONV):
@@ -215,6 +266,94 @@ class Operator:
         if getattr(self, "ctx", None) is not None and self.ctx.value:
             self.lib.ceedbp_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def kappa_misfit(kappa, op: "Operator", b, u_star, tol: float = 1e-10):
+    """J(kappa) = 1/2 ||u(kappa) - u*||_B^2 with A(kappa) u = b, differentiable in kappa.
+
+    The backward pass returns dJ/dkappa from one adjoint solve and the fused
+    gradient kernel (ceedbp_kappa_gradient)."""
+    import torch
+
+    class _KappaMisfit(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, k):
+            op.set_kappa(k.detach().contiguous())
+            u, _ = op.solve(b, tol=tol)
+            rhs, J = op.misfit(u, u_star)
+            lam, _ = op.solve(rhs, tol=tol)
+            ctx.save_for_backward(op.kappa_gradient(u, lam))
+            return torch.tensor(J, dtype=torch.float64, device=k.device)
+
+        @staticmethod
+        def backward(ctx, grad_J):
+            (g,) = ctx.saved_tensors
+            return grad_J * g
+
+    return _KappaMisfit.apply(kappa)
+
+
+class Batch:
+    """Many independent BP5 problems solved together (ceedbp_batch_setup / _solve)."""
+
+    def __init__(self, problems, stream=None, device=None):
+        """problems: list of (order, coords, l2g, dirichlet) as returned by mesh_box."""
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("ceedbp needs a CUDA device; there is no CPU path")
+        self.lib = load_library()
+        self.device = torch.device("cuda") if device is None else torch.device(device)
+        self.stream = torch.cuda.Stream(self.device) if stream is None else stream
+        n = len(problems)
+        self._keep = []
+        prm = (Params * n)()
+        cp, lp, dp = (_P * n)(), (_P * n)(), (_P * n)()
+        self.sizes = []
+        for k, (order, coords, l2g, dirichlet) in enumerate(problems):
+            coords = np.ascontiguousarray(coords, dtype=np.float64)
+            l2g = np.ascontiguousarray(l2g, dtype=np.int64)
+            dirichlet = np.ascontiguousarray(dirichlet, dtype=np.uint8)
+            self._keep += [coords, l2g, dirichlet]
+            prm[k] = Params(5, order, 0, coords.shape[0], dirichlet.shape[0], ARITH_DF64)
+            cp[k], lp[k], dp[k] = _ptr(coords), _ptr(l2g), _ptr(dirichlet)
+            self.sizes.append((order, coords.shape[0], dirichlet.shape[0]))
+        out = ctypes.c_void_p()
+        torch.cuda.current_stream(self.device).synchronize()
+        st = self.lib.ceedbp_batch_setup(n, prm, cp, lp, dp, ctypes.c_void_p(self.stream.cuda_stream),
+                                         ctypes.byref(out))
+        self._keep = []
+        if st != OK:
+            raise CeedbpError(st, (self.lib.ceedbp_batch_last_error(None) or b"").decode())
+        self.handle = out
+        self.n = n
+
+    def solve(self, bs, xs=None, tol: float = 1e-8, maxit: int = 10000, chunk: int = 32, use_graph: bool = True):
+        import torch
+        xs = [torch.empty_like(b) for b in bs] if xs is None else xs
+        bp, xp = (_P * self.n)(), (_P * self.n)()
+        for k in range(self.n):
+            bp[k] = ctypes.c_void_p(bs[k].data_ptr())
+            xp[k] = ctypes.c_void_p(xs[k].data_ptr())
+        opts = SolveOpts(tol, maxit, 0, chunk, int(use_graph), 0, 0, 0, 0.0, 0, 0)
+        infos = (SolveInfo * self.n)()
+        cur = torch.cuda.current_stream(self.device)
+        self.stream.wait_stream(cur)
+        st = self.lib.ceedbp_batch_solve(self.handle, bp, xp, ctypes.byref(opts), infos)
+        cur.wait_stream(self.stream)
+        if st not in (OK,):
+            raise CeedbpError(st, (self.lib.ceedbp_batch_last_error(self.handle) or b"").decode())
+        return xs, [infos[k].as_dict(1) for k in range(self.n)]
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            self.lib.ceedbp_batch_destroy(self.handle)
+            self.handle = None
 
     def __del__(self):
         try:

@@ -8,6 +8,7 @@
 #include <string>
 #include <vector>
 
+#include "kernel_args.h"
 #include "internal.h"
 
 namespace ceedbp {
@@ -68,9 +69,13 @@ void release(ceedbp_ctx* c) {
   for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
   c->graphs.clear();
   void* ptrs[] = {c->d_l2g, c->d_off, c->d_slots, c->d_basis, c->d_G, c->d_Mq, c->d_dinv, c->d_mdiag,
-                  c->d_wl, c->d_r, c->d_p, c->d_ax, c->d_part_apply, c->d_part_vec, c->d_state};
+                  c->d_wl, c->d_r, c->d_p, c->d_ax, c->d_part_apply, c->d_part_vec, c->d_state,
+                  c->d_Gdf, c->d_Ddf, c->d_dinvdf, c->d_G32, c->d_Gbf, c->d_dinv32, c->d_xin,
+                  c->d_rin, c->d_pin, c->d_outer, c->d_Ghat, c->d_scal};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  if (c->h_outer) cudaFreeHost(c->h_outer);
+  if (c->h_scal) cudaFreeHost(c->h_scal);
   if (c->h_state) cudaFreeHost(c->h_state);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
@@ -102,6 +107,10 @@ ceedbp_status setup_impl(ceedbp_ctx* c, const double* coords, const int64_t* l2g
   if (nloc >= (int64_t(1) << 31) || P.nglobal >= (int64_t(1) << 31) - 1)
     return fail(c, CEEDBP_EINVAL, "problem too large for 32-bit local indices (E p1^3 and nglobal must stay below 2^31)");
   const bool masked = P.bp != 1 && dirichlet != nullptr;
+  if (P.arith != CEEDBP_ARITH_FP64 && P.arith != CEEDBP_ARITH_DF64) return fail(c, CEEDBP_EINVAL, "unknown arith");
+  if (P.arith == CEEDBP_ARITH_DF64 && !gll_quad)
+    return fail(c, CEEDBP_EUNSUPPORTED, "the FP32-pair arithmetic is built for BP5 and BP6 only");
+  c->arith = P.arith;
 
   // ---- host: encoded l2g, CSR of local slots per global node (counting sort, slots ascending)
   std::vector<int> hl2g(nloc), hoff(P.nglobal + 1, 0), hslots(nloc);
@@ -142,6 +151,8 @@ ceedbp_status setup_impl(ceedbp_ctx* c, const double* coords, const int64_t* l2g
   CK(c, dalloc(&c->d_p, size_t(n) * nc));
   CK(c, dalloc(&c->d_ax, size_t(n) * nc));
   CK(c, dalloc(&c->d_state, 1));
+  CK(c, dalloc(&c->d_scal, 4));
+  CK(c, cudaMallocHost(reinterpret_cast<void**>(&c->h_scal), 4 * sizeof(double)));
   CK(c, cudaMallocHost(reinterpret_cast<void**>(&c->h_state), sizeof(SolveState)));
   CK(c, cudaEventCreate(&c->ev0));
   CK(c, cudaEventCreate(&c->ev1));
@@ -165,7 +176,8 @@ ceedbp_status setup_impl(ceedbp_ctx* c, const double* coords, const int64_t* l2g
   m.slots = c->d_slots;
   m.basis = c->d_basis;
 
-  const int nb_apply = elem_blocks(m);
+  int nb_apply = elem_blocks(m);
+  if (c->colloc) nb_apply = std::max(nb_apply, std::max(int(P.nelem), elem_lp_blocks(m)));
   CK(c, dalloc(&c->d_part_apply, size_t(nb_apply) * nc));
   CK(c, dalloc(&c->d_part_vec, size_t(vec_blocks(n)) * 3 * nc));
 
@@ -181,7 +193,15 @@ ceedbp_status setup_impl(ceedbp_ctx* c, const double* coords, const int64_t* l2g
       CK(c, dalloc(&d_kappa, size_t(P.nelem) * Q3));
       CK(c, cudaMemcpyAsync(d_kappa, kappa, sizeof(double) * P.nelem * Q3, cudaMemcpyHostToDevice, s));
     }
-    cudaError_t e = launch_geom(m, d_coords, d_kappa, c->d_G, c->d_Mq, d_scratch, s);
+    cudaError_t e = cudaSuccess;
+    if (d_kappa) {
+      // keep the coefficient-free factors for ceedbp_set_kappa and the adjoint gradient
+      e = dalloc(&c->d_Ghat, size_t(P.nelem) * 6 * Q3);
+      if (e == cudaSuccess) e = launch_geom(m, d_coords, nullptr, c->d_Ghat, c->d_Mq, d_scratch, s);
+      if (e == cudaSuccess) e = launch_scale_factors(c->d_Ghat, d_kappa, c->d_G, P.nelem, int(Q3), s);
+    } else {
+      e = launch_geom(m, d_coords, nullptr, c->d_G, c->d_Mq, d_scratch, s);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(d_coords);
     cudaFree(d_scratch);
@@ -219,14 +239,116 @@ ceedbp_status setup_impl(ceedbp_ctx* c, const double* coords, const int64_t* l2g
       CK(c, launch_elem(m, kMass, a, s));
     }
   }
+  if (c->arith == CEEDBP_ARITH_DF64) {
+    // pair copies of G, D and dinv; splitter bounds from the row and column sums of |D|
+    const size_t ng = size_t(P.nelem) * 6 * Q3;
+    CK(c, dalloc(&c->d_Gdf, ng));
+    CK(c, dalloc(&c->d_Ddf, size_t(p1) * p1));
+    CK(c, dalloc(&c->d_dinvdf, n));
+    CK(c, launch_f64_to_df(c->d_G, c->d_Gdf, int64_t(ng), s));
+    CK(c, launch_f64_to_df(c->d_dinv, c->d_dinvdf, n, s));
+    std::vector<dfloat> hd(size_t(p1) * p1);
+    double rmax = 0.0, cmax = 0.0;
+    for (int a = 0; a < p1; ++a) {
+      double rs = 0.0, cs = 0.0;
+      for (int b = 0; b < p1; ++b) {
+        const double d = basis.Dq[size_t(a) * p1 + b];
+        const float hi = float(d);
+        hd[size_t(a) * p1 + b] = dfloat{hi, float(d - double(hi))};
+        rs += std::fabs(d);
+        cs += std::fabs(basis.Dq[size_t(b) * p1 + a]);
+      }
+      rmax = std::max(rmax, rs);
+      cmax = std::max(cmax, cs);
+    }
+    c->dnorm_row = float(rmax * (1.0 + 1e-6));
+    c->dnorm_col = float(cmax * (1.0 + 1e-6));
+    CK(c, cudaMemcpyAsync(c->d_Ddf, hd.data(), sizeof(dfloat) * hd.size(), cudaMemcpyHostToDevice, s));
+    CK(c, set_df_dconst(p1, hd.data(), s));
+    CK(c, cudaStreamSynchronize(s));
+    ElemDfArgs a{};
+    a.u_f64 = c->d_r;
+    a.wl = reinterpret_cast<dfloat*>(c->d_wl);
+    a.G = c->d_Gdf;
+    a.D = c->d_Ddf;
+    a.dnorm_row = c->dnorm_row;
+    a.dnorm_col = c->dnorm_col;
+    a.mask_in = 1;
+    a.fault = &c->d_state->fault;
+    CK(c, launch_elem_df(m, a, s));
+    CK(c, cudaStreamSynchronize(s));
+    // autotuner: elements per block of the pair kernel, timed on this mesh
+    const int max_eb = elem_df_max_tile(m);
+    if (max_eb > 1) {
+      float best = 1e30f;
+      int best_eb = 1;
+      for (int eb = 1; eb <= max_eb; ++eb) {
+        m.tune_eb = eb;
+        CK(c, launch_elem_df(m, a, s));  // warm-up of this shape
+        CK(c, cudaEventRecord(c->ev0, s));
+        for (int r = 0; r < 3; ++r) CK(c, launch_elem_df(m, a, s));
+        CK(c, cudaEventRecord(c->ev1, s));
+        CK(c, cudaEventSynchronize(c->ev1));
+        float ms = 0.0f;
+        CK(c, cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+        if (ms < best) {
+          best = ms;
+          best_eb = eb;
+        }
+      }
+      m.tune_eb = best_eb;
+    } else {
+      m.tune_eb = 1;
+    }
+    CK(c, cudaMemsetAsync(&c->d_state->fault, 0, sizeof(int), s));
+  }
   CK(c, cudaStreamSynchronize(s));
   return CEEDBP_OK;
+}
+
+}  // namespace
+
+namespace ceedbp {
+ceedbp_status setup_context(ceedbp_ctx* c, const double* coords, const int64_t* l2g, const uint8_t* dirichlet,
+                            const double* kappa) {
+  return setup_impl(c, coords, l2g, dirichlet, kappa);
+}
+void release_context(ceedbp_ctx* c) { release(c); }
+}  // namespace ceedbp
+
+namespace {
+
+ElemDfArgs df_args(ceedbp_ctx* c) {
+  ElemDfArgs a{};
+  a.fault = &c->d_state->fault;
+  a.G = c->d_Gdf;
+  a.D = c->d_Ddf;
+  a.dnorm_row = c->dnorm_row;
+  a.dnorm_col = c->dnorm_col;
+  a.wl = reinterpret_cast<dfloat*>(c->d_wl);
+  return a;
 }
 
 // Events recorded inside a capture become event-record nodes of the graph.
 void mark(ceedbp_ctx* c, int i, bool capturing) {
   if (capturing) cudaEventRecordWithFlags(c->prof[i], c->stream, cudaEventRecordExternal);
   else cudaEventRecord(c->prof[i], c->stream);
+}
+
+void run_inner_iterations(ceedbp_ctx* c, int bf16, int n) {
+  const DeviceMesh& m = c->mesh;
+  ElemLpArgs a{};
+  a.u = c->d_pin;
+  a.wl = reinterpret_cast<float*>(c->d_wl);
+  a.G = bf16 ? c->d_Gbf : static_cast<const void*>(c->d_G32);
+  a.partials = c->d_part_apply;
+  a.state = c->d_state;
+  for (int i = 0; i < n; ++i) {
+    launch_elem_lp(m, a, bf16, c->stream);
+    launch_inner_update(m, bf16, a.wl, c->d_xin, c->d_rin, c->d_pin, c->d_dinv32, c->d_part_vec, c->d_state,
+                        c->stream);
+    launch_inner_dir(m, bf16, c->d_rin, c->d_pin, c->d_dinv32, c->d_state, c->stream);
+  }
 }
 
 void run_iterations(ceedbp_ctx* c, double* x, int n, bool profile = false, bool capturing = false) {
@@ -239,13 +361,26 @@ void run_iterations(ceedbp_ctx* c, double* x, int n, bool profile = false, bool 
   a.state = c->d_state;
   a.mask_in = 0;  // p is zero on Dirichlet nodes
   a.skip_dirichlet_out = 1;
+  ElemDfArgs da = df_args(c);
+  da.u_df = reinterpret_cast<const dfloat*>(c->d_p);
+  da.partials = c->d_part_apply;
+  da.state = c->d_state;
+  da.skip_dirichlet_out = 1;
+  dfloat* xd = reinterpret_cast<dfloat*>(c->d_ax);
+  dfloat* rd = reinterpret_cast<dfloat*>(c->d_r);
+  dfloat* pd = reinterpret_cast<dfloat*>(c->d_p);
+  const dfloat* wd = reinterpret_cast<const dfloat*>(c->d_wl);
+  const bool df = c->arith == CEEDBP_ARITH_DF64;
   for (int i = 0; i < n; ++i) {
     if (profile) mark(c, 4 * i + 0, capturing);
-    launch_elem(m, c->op_kind, a, c->stream);
+    if (df) launch_elem_df(m, da, c->stream);
+    else launch_elem(m, c->op_kind, a, c->stream);
     if (profile) mark(c, 4 * i + 1, capturing);
-    launch_pcg_update(m, c->d_wl, x, c->d_r, c->d_p, c->d_dinv, c->d_part_vec, c->d_state, c->stream);
+    if (df) launch_update_df(m, wd, xd, rd, pd, c->d_dinvdf, c->d_part_vec, c->d_state, c->stream);
+    else launch_pcg_update(m, c->d_wl, x, c->d_r, c->d_p, c->d_dinv, c->d_part_vec, c->d_state, c->stream);
     if (profile) mark(c, 4 * i + 2, capturing);
-    launch_pcg_dir(m, c->d_r, c->d_p, c->d_dinv, c->d_state, c->stream);
+    if (df) launch_dir_df(m, rd, pd, c->d_dinvdf, c->d_state, c->stream);
+    else launch_pcg_dir(m, c->d_r, c->d_p, c->d_dinv, c->d_state, c->stream);
     if (profile) mark(c, 4 * i + 3, capturing);
   }
 }
@@ -259,15 +394,16 @@ ceedbp_status ensure_prof_events(ceedbp_ctx* c, int n) {
   return CEEDBP_OK;
 }
 
-ceedbp_status graph_for(ceedbp_ctx* c, double* x, int n, int profile, cudaGraphExec_t* out) {
+ceedbp_status graph_for(ceedbp_ctx* c, double* x, int n, int profile, cudaGraphExec_t* out, int mode = 0) {
   for (auto& g : c->graphs)
-    if (g.x == x && g.n == n && g.profile == profile) {
+    if (g.x == x && g.n == n && g.profile == profile && g.mode == mode) {
       *out = g.exec;
       return CEEDBP_OK;
     }
   cudaGraph_t graph = nullptr;
   CK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-  run_iterations(c, x, n, profile != 0, true);
+  if (mode == 0) run_iterations(c, x, n, profile != 0, true);
+  else run_inner_iterations(c, mode == 2, n);
   cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
   cudaGraphExec_t exec = nullptr;
@@ -278,14 +414,152 @@ ceedbp_status graph_for(ceedbp_ctx* c, double* x, int n, int profile, cudaGraphE
     cudaGraphExecDestroy(c->graphs.front().exec);
     c->graphs.erase(c->graphs.begin());
   }
-  c->graphs.push_back({x, n, profile, exec});
+  c->graphs.push_back({x, n, profile, mode, exec});
   *out = exec;
   return CEEDBP_OK;
+}
+
+ceedbp_status solve_mixed(ceedbp_ctx* c, const double* b, double* x, const ceedbp_solve_opts& o,
+                          ceedbp_solve_info* info) {
+  const int bf16 = o.mixed == CEEDBP_MIXED_BF16 ? 1 : 0;
+  if (o.mixed != CEEDBP_MIXED_FP32 && o.mixed != CEEDBP_MIXED_BF16) return fail(c, CEEDBP_EINVAL, "unknown mixed mode");
+  if (!c->colloc) return fail(c, CEEDBP_EUNSUPPORTED, "defect correction is built for BP5 and BP6");
+  if ((bf16 && !c->d_Gbf) || (!bf16 && !c->d_G32) || !c->d_xin)
+    return fail(c, CEEDBP_EINVAL, "call ceedbp_prepare_mixed for this precision first");
+  const int nc = c->ncomp;
+  const int64_t n = c->prm.nglobal;
+  cudaStream_t s = c->stream;
+  const double inner_tol = o.inner_tol > 0.0 ? o.inner_tol : (bf16 ? 3e-3 : 1e-4);
+  const int inner_maxit = o.inner_maxit > 0 ? o.inner_maxit : o.maxit;
+  const int outer_maxit = o.outer_maxit > 0 ? o.outer_maxit : 50;
+  const bool graphs = o.use_graph && s != nullptr;
+  unsigned* ticket = &c->d_state->ticket[kTicketResidual];
+  // ||b||
+  CK(c, launch_residual(c->mesh, b, nullptr, c->d_r, c->d_part_vec, ticket, c->d_outer, s));
+  CK(c, cudaMemcpyAsync(c->h_outer, c->d_outer, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(c, cudaStreamSynchronize(s));
+  double bb[3] = {0, 0, 0}, rr[3] = {0, 0, 0};
+  for (int k = 0; k < nc; ++k) bb[k] = rr[k] = c->h_outer[k];
+  if (o.x0_nonzero) {
+    ceedbp_status st = ceedbp_apply(c, x, c->d_ax);
+    if (st != CEEDBP_OK) return st;
+    CK(c, launch_residual(c->mesh, b, c->d_ax, c->d_r, c->d_part_vec, ticket, c->d_outer, s));
+    CK(c, cudaMemcpyAsync(c->h_outer, c->d_outer, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(c, cudaStreamSynchronize(s));
+    for (int k = 0; k < nc; ++k) rr[k] = c->h_outer[k];
+  } else {
+    CK(c, cudaMemsetAsync(x, 0, sizeof(double) * n * nc, s));
+  }
+  CK(c, cudaEventRecord(c->ev0, s));
+  int outer = 0, inner_total[3] = {0, 0, 0};
+  ceedbp_status result = CEEDBP_OK;
+  while (true) {
+    bool done = true;
+    for (int k = 0; k < nc; ++k)
+      if (rr[k] > o.tol * o.tol * bb[k]) done = false;
+    if (done) break;
+    if (outer >= outer_maxit) {
+      result = CEEDBP_ENOCONV;
+      break;
+    }
+    double scale[3] = {0, 0, 0}, norm[3] = {0, 0, 0};
+    for (int k = 0; k < nc; ++k) {
+      norm[k] = std::sqrt(rr[k]);
+      scale[k] = norm[k] > 0.0 ? 1.0 / norm[k] : 0.0;
+    }
+    CK(c, launch_inner_init(c->mesh, bf16, c->d_r, scale, c->d_dinv32, c->d_xin, c->d_rin, c->d_pin, c->d_part_vec,
+                            c->d_state, inner_tol, s));
+    int its = 0;
+    while (its < inner_maxit) {
+      const int k = std::min(o.chunk, inner_maxit - its);
+      if (graphs) {
+        cudaGraphExec_t exec = nullptr;
+        ceedbp_status st = graph_for(c, nullptr, k, 0, &exec, bf16 ? 2 : 1);
+        if (st != CEEDBP_OK) return st;
+        CK(c, cudaGraphLaunch(exec, s));
+      } else {
+        run_inner_iterations(c, bf16, k);
+        CK(c, cudaGetLastError());
+      }
+      CK(c, cudaMemcpyAsync(c->h_state, c->d_state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+      CK(c, cudaStreamSynchronize(s));
+      its += k;
+      if (c->h_state->stop) break;
+    }
+    for (int k = 0; k < nc; ++k) {
+      inner_total[k] += c->h_state->c[k].iters;
+      if (c->h_state->c[k].status == CEEDBP_EBREAKDOWN) result = CEEDBP_EBREAKDOWN;
+    }
+    if (result == CEEDBP_EBREAKDOWN) break;
+    CK(c, launch_correct(c->mesh, x, c->d_xin, norm, s));
+    ceedbp_status st = ceedbp_apply(c, x, c->d_ax);
+    if (st != CEEDBP_OK) return st;
+    CK(c, launch_residual(c->mesh, b, c->d_ax, c->d_r, c->d_part_vec, ticket, c->d_outer, s));
+    CK(c, cudaMemcpyAsync(c->h_outer, c->d_outer, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(c, cudaStreamSynchronize(s));
+    for (int k = 0; k < nc; ++k) rr[k] = c->h_outer[k];
+    ++outer;
+  }
+  CK(c, cudaEventRecord(c->ev1, s));
+  CK(c, cudaEventSynchronize(c->ev1));
+  float ms = 0.0f;
+  CK(c, cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    for (int k = 0; k < nc; ++k) {
+      info->iters[k] = inner_total[k];
+      info->res_norm[k] = std::sqrt(rr[k]);
+      info->b_norm[k] = std::sqrt(bb[k]);
+      info->rel_res[k] = bb[k] > 0.0 ? std::sqrt(rr[k] / bb[k]) : 0.0;
+    }
+    info->device_ms = ms;
+    info->outer_iters = outer;
+    info->status = result;
+  }
+  if (result == CEEDBP_ENOCONV) c->err = "defect correction: outer_maxit reached before the tolerance";
+  if (result == CEEDBP_EBREAKDOWN) c->err = "defect correction: inner CG breakdown";
+  return result;
 }
 
 }  // namespace
 
 extern "C" {
+
+ceedbp_status ceedbp_prepare_mixed(ceedbp_ctx* c, int precision) {
+  if (!c) return fail(c, CEEDBP_EINVAL, "null context");
+  if (precision != CEEDBP_MIXED_FP32 && precision != CEEDBP_MIXED_BF16)
+    return fail(c, CEEDBP_EINVAL, "precision must be CEEDBP_MIXED_FP32 or CEEDBP_MIXED_BF16");
+  if (!c->colloc) return fail(c, CEEDBP_EUNSUPPORTED, "defect correction is built for BP5 and BP6");
+  const int64_t n = c->prm.nglobal, nc = c->ncomp;
+  const int64_t ng = c->prm.nelem * 6 * int64_t(c->q) * c->q * c->q;
+  cudaStream_t s = c->stream;
+  if (!c->d_xin) {
+    CK(c, dalloc(&c->d_xin, size_t(n * nc)));
+    CK(c, dalloc(&c->d_rin, size_t(n * nc)));
+    CK(c, dalloc(reinterpret_cast<float**>(&c->d_pin), size_t(n * nc)));
+    CK(c, dalloc(&c->d_dinv32, size_t(n)));
+    CK(c, dalloc(&c->d_outer, 3));
+    CK(c, cudaMallocHost(reinterpret_cast<void**>(&c->h_outer), 3 * sizeof(double)));
+    CK(c, launch_narrow(c->d_dinv, c->d_dinv32, n, 0, s));
+  }
+  if (precision == CEEDBP_MIXED_FP32 && !c->d_G32) {
+    CK(c, dalloc(&c->d_G32, size_t(ng)));
+    CK(c, launch_narrow(c->d_G, c->d_G32, ng, 0, s));
+  }
+  if (precision == CEEDBP_MIXED_BF16 && !c->d_Gbf) {
+    CK(c, cudaMalloc(&c->d_Gbf, sizeof(uint16_t) * size_t(ng)));
+    CK(c, launch_narrow(c->d_G, c->d_Gbf, ng, 1, s));
+  }
+  // prime the inner element kernel outside any capture (one-time attribute setup)
+  ElemLpArgs a{};
+  a.u = c->d_pin;
+  a.wl = reinterpret_cast<float*>(c->d_wl);
+  a.G = precision == CEEDBP_MIXED_BF16 ? c->d_Gbf : static_cast<const void*>(c->d_G32);
+  CK(c, cudaMemsetAsync(c->d_pin, 0, sizeof(float) * size_t(n * nc), s));
+  CK(c, launch_elem_lp(c->mesh, a, precision == CEEDBP_MIXED_BF16, s));
+  CK(c, cudaStreamSynchronize(s));
+  return CEEDBP_OK;
+}
 
 ceedbp_status ceedbp_setup(const ceedbp_params* params, const double* coords, const int64_t* l2g,
                            const uint8_t* dirichlet, const double* kappa, void* stream, ceedbp_ctx** out) {
@@ -308,6 +582,15 @@ ceedbp_status ceedbp_setup(const ceedbp_params* params, const double* coords, co
 
 ceedbp_status ceedbp_apply(ceedbp_ctx* c, const double* u, double* w) {
   if (!c || !u || !w) return fail(c, CEEDBP_EINVAL, "null argument");
+  if (c->arith == CEEDBP_ARITH_DF64) {
+    ElemDfArgs da = df_args(c);
+    da.u_f64 = u;
+    da.mask_in = 1;
+    da.skip_dirichlet_out = 1;
+    CK(c, launch_elem_df(c->mesh, da, c->stream));
+    CK(c, launch_gs_df(c->mesh, reinterpret_cast<const dfloat*>(c->d_wl), w, 1, c->stream));
+    return CEEDBP_OK;
+  }
   ElemArgs a{};
   a.u = u;
   a.wl = c->d_wl;
@@ -345,11 +628,12 @@ ceedbp_status ceedbp_jacobi(ceedbp_ctx* c, double* dinv) {
 ceedbp_status ceedbp_solve(ceedbp_ctx* c, const double* b, double* x, const ceedbp_solve_opts* opts,
                            ceedbp_solve_info* info) {
   if (!c || !b || !x) return fail(c, CEEDBP_EINVAL, "null argument");
-  ceedbp_solve_opts o{1e-8, 10000, 0, 32, 1, 0, 0};
+  ceedbp_solve_opts o{1e-8, 10000, 0, 32, 1, 0, 0, 0, 0.0, 0, 0};
   if (opts) o = *opts;
   if (o.chunk <= 0) o.chunk = 32;
   if (o.maxit <= 0) o.maxit = 10000;
   if (!(o.tol >= 0.0)) return fail(c, CEEDBP_EINVAL, "tol must be >= 0");
+  if (o.mixed != CEEDBP_MIXED_NONE) return solve_mixed(c, b, x, o, info);
   const int nc = c->ncomp;
   const int64_t n = c->prm.nglobal;
   cudaStream_t s = c->stream;
@@ -362,7 +646,13 @@ ceedbp_status ceedbp_solve(ceedbp_ctx* c, const double* b, double* x, const ceed
     CK(c, cudaMemsetAsync(x, 0, sizeof(double) * n * nc, s));
   }
   const int fixed = o.fixed_iters > 0 ? 1 : 0;
-  CK(c, launch_pcg_init(c->mesh, b, ax, x, c->d_r, c->d_p, c->d_dinv, c->d_part_vec, c->d_state, o.tol, fixed, s));
+  const bool df = c->arith == CEEDBP_ARITH_DF64;
+  if (df)
+    CK(c, launch_init_df(c->mesh, b, ax, x, reinterpret_cast<dfloat*>(c->d_ax), reinterpret_cast<dfloat*>(c->d_r),
+                         reinterpret_cast<dfloat*>(c->d_p), c->d_dinvdf, o.x0_nonzero, c->d_part_vec, c->d_state,
+                         o.tol, fixed, s));
+  else
+    CK(c, launch_pcg_init(c->mesh, b, ax, x, c->d_r, c->d_p, c->d_dinv, c->d_part_vec, c->d_state, o.tol, fixed, s));
   const int limit = fixed ? o.fixed_iters : o.maxit;
   const bool graphs = o.use_graph && s != nullptr;
   const bool profile = o.profile != 0;
@@ -401,10 +691,18 @@ ceedbp_status ceedbp_solve(ceedbp_ctx* c, const double* b, double* x, const ceed
     done += k;
     if (c->h_state->stop) break;
   }
+  if (df) {
+    CK(c, launch_df_to_f64(reinterpret_cast<const dfloat*>(c->d_ax), x, n * nc, s));
+    CK(c, cudaStreamSynchronize(s));
+  }
   float ms = 0.0f;
   CK(c, cudaEventElapsedTime(&ms, c->ev0, c->ev1));
   ceedbp_status result = CEEDBP_OK;
   const SolveState& h = *c->h_state;
+  if (h.fault) {
+    c->err = "a kernel gave up a bounded wait for its staging copy; results are invalid";
+    return CEEDBP_ECUDA;
+  }
   for (int comp = 0; comp < nc; ++comp) {
     if (h.c[comp].status == CEEDBP_EBREAKDOWN) result = CEEDBP_EBREAKDOWN;
     else if (!fixed && h.c[comp].active && result == CEEDBP_OK) result = CEEDBP_ENOCONV;
@@ -425,6 +723,53 @@ ceedbp_status ceedbp_solve(ceedbp_ctx* c, const double* b, double* x, const ceed
   if (result == CEEDBP_EBREAKDOWN) c->err = "CG breakdown (p^T A p <= 0 or non-finite scalar)";
   if (result == CEEDBP_ENOCONV) c->err = "maxit reached before the tolerance";
   return result;
+}
+
+ceedbp_status ceedbp_set_kappa(ceedbp_ctx* c, const double* kappa) {
+  if (!c || !kappa) return fail(c, CEEDBP_EINVAL, "null argument");
+  if (c->op_kind != kStiff) return fail(c, CEEDBP_EUNSUPPORTED, "kappa applies to stiffness problems");
+  cudaStream_t s = c->stream;
+  const int64_t q3 = int64_t(c->q) * c->q * c->q;
+  const size_t ng = size_t(c->prm.nelem) * 6 * q3;
+  if (!c->d_Ghat) {  // set up with kappa = 1: the current factors are coefficient-free
+    CK(c, dalloc(&c->d_Ghat, ng));
+    CK(c, cudaMemcpyAsync(c->d_Ghat, c->d_G, sizeof(double) * ng, cudaMemcpyDeviceToDevice, s));
+  }
+  CK(c, launch_scale_factors(c->d_Ghat, kappa, c->d_G, c->prm.nelem, int(q3), s));
+  const DeviceMesh& m = c->mesh;
+  CK(c, launch_local_diag(m, kStiff, c->d_G, c->d_Mq, c->d_wl, s));
+  DeviceMesh m1 = m;
+  m1.ncomp = 1;
+  CK(c, launch_gs(m1, c->d_wl, c->d_r, 0, s));
+  CK(c, launch_dinv(c->d_off, c->d_r, c->d_dinv, c->prm.nglobal, s));
+  if (c->d_Gdf) {
+    CK(c, launch_f64_to_df(c->d_G, c->d_Gdf, int64_t(ng), s));
+    CK(c, launch_f64_to_df(c->d_dinv, c->d_dinvdf, c->prm.nglobal, s));
+  }
+  if (c->d_G32) CK(c, launch_narrow(c->d_G, c->d_G32, int64_t(ng), 0, s));
+  if (c->d_Gbf) CK(c, launch_narrow(c->d_G, c->d_Gbf, int64_t(ng), 1, s));
+  if (c->d_dinv32) CK(c, launch_narrow(c->d_dinv, c->d_dinv32, c->prm.nglobal, 0, s));
+  return CEEDBP_OK;
+}
+
+ceedbp_status ceedbp_misfit(ceedbp_ctx* c, const double* u, const double* ustar, double* rhs, double* J) {
+  if (!c || !u || !ustar || !rhs) return fail(c, CEEDBP_EINVAL, "null argument");
+  if (!c->colloc || c->ncomp != 1) return fail(c, CEEDBP_EUNSUPPORTED, "misfit is built for BP5");
+  cudaStream_t s = c->stream;
+  CK(c, launch_misfit(c->mesh, c->d_mdiag, u, ustar, rhs, c->d_part_vec, &c->d_state->ticket[kTicketResidual],
+                      c->d_scal, s));
+  CK(c, cudaMemcpyAsync(c->h_scal, c->d_scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(c, cudaStreamSynchronize(s));
+  if (J) *J = c->h_scal[0];
+  return CEEDBP_OK;
+}
+
+ceedbp_status ceedbp_kappa_gradient(ceedbp_ctx* c, const double* u, const double* lam, double* g) {
+  if (!c || !u || !lam || !g) return fail(c, CEEDBP_EINVAL, "null argument");
+  if (!c->colloc || c->ncomp != 1) return fail(c, CEEDBP_EUNSUPPORTED, "the adjoint gradient is built for BP5");
+  if (c->p1 > 12) return fail(c, CEEDBP_EUNSUPPORTED, "the adjoint gradient is built for orders 1..11");
+  CK(c, launch_kappa_grad(c->mesh, u, lam, c->d_Ghat ? c->d_Ghat : c->d_G, g, c->stream));
+  return CEEDBP_OK;
 }
 
 ceedbp_status ceedbp_destroy(ceedbp_ctx* c) {

@@ -4,12 +4,14 @@
 #include <string>
 #include <vector>
 
+#include "df.cuh"
 #include "internal.h"
 
 struct GraphEntry {
   double* x;
   int n;
   int profile;
+  int mode;  // 0: FP64 / pair iteration, 1: FP32 inner, 2: BF16 inner
   cudaGraphExec_t exec;
 };
 
@@ -31,6 +33,27 @@ struct ceedbp_ctx {
   double* d_r = nullptr;
   double* d_p = nullptr;
   double* d_ax = nullptr;
+  // FP32-pair path (arith == CEEDBP_ARITH_DF64): pair copies of G, D and the
+  // Jacobi inverse; the CG pair vectors reuse d_r, d_p, d_ax and the local
+  // scratch d_wl (a pair has the size of a double).
+  int arith = 0;
+  ceedbp::dfloat* d_Gdf = nullptr;
+  ceedbp::dfloat* d_Ddf = nullptr;
+  ceedbp::dfloat* d_dinvdf = nullptr;
+  float dnorm_row = 0.0f, dnorm_col = 0.0f;
+  // defect correction: low-precision G copies, FP32 inner vectors, outer norms
+  float* d_G32 = nullptr;
+  void* d_Gbf = nullptr;
+  float* d_dinv32 = nullptr;
+  float* d_xin = nullptr;
+  float* d_rin = nullptr;
+  void* d_pin = nullptr;  // n * ncomp * 4 bytes (FP32 or BF16 direction)
+  double* d_outer = nullptr;
+  double* h_outer = nullptr;
+  // variable coefficient: coefficient-free factors (kept when kappa is used)
+  double* d_Ghat = nullptr;
+  double* d_scal = nullptr;  // small device outputs (misfit)
+  double* h_scal = nullptr;
   double* d_part_apply = nullptr;
   double* d_part_vec = nullptr;
   ceedbp::SolveState* d_state = nullptr;

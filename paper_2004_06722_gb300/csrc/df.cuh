@@ -1,6 +1,6 @@
 // Double-float arithmetic: a value is an unevaluated pair (hi, lo) of FP32
-// numbers, hi + lo.  The GB300 issues FP32 FMAs 64 times faster than FP64 ones,
-// so FP64-accurate contractions run on pairs of FP32 numbers.
+// numbers, hi + lo.  The GB300 issues FP32 FMAs about 60 times faster than
+// FP64 ones, so FP64-accurate contractions run on pairs of FP32 numbers.
 //
 // Building blocks (Dekker 1971; Knuth TAOCP vol. 2; Joldes, Muller and Popescu,
 // ACM TOMS 44(2), 2017):
@@ -11,8 +11,9 @@
 //
 // Splitter accumulation: for a sum s = sum_n D_n x_n whose partial sums are
 // bounded by B, pick sigma = 2^k >= 2B.  Then A = sigma + partial stays in
-// [sigma/2, 3 sigma/2]; every step A' = fl(D x + A) rounds on a fixed grid, the
-// step A - A' is exact (Sterbenz) and fl(D x + (A - A')) recovers its rounding
+// [sigma/2, 3 sigma/2] where every float is a multiple of 2^-24 sigma; each step
+// A' = fl(D x + A) rounds on that grid, the step A - A' is exact (a multiple of
+// the grid below sigma in size) and fl(D x + (A - A')) recovers its rounding
 // error to 2^-24 of one grid unit.  The exact grid part accumulates in A and
 // the small parts in a plain float, 6 FP32 instructions per pair product
 // instead of 12 for a two_sum-based pair dot (same idea as the error-free
@@ -97,20 +98,61 @@ __device__ __forceinline__ float splitter(float b) {
   return __uint_as_float(bits);
 }
 
-// Accumulator of sum D x over pairs with a fixed splitter sigma.
+// Accumulator of sum D x over pairs with a fixed splitter sigma.  The grid
+// part accumulates in A, the rounding errors of the grid steps in s and the
+// cross terms dh*xl + dl*xh in c (separate chains keep the dependency depth
+// at two instructions per term).
 struct SplitAcc {
-  float A, s;
-  __device__ __forceinline__ explicit SplitAcc(float sigma) : A(sigma), s(0.0f) {}
+  float A, s, c;
+  __device__ __forceinline__ explicit SplitAcc(float sigma) : A(sigma), s(0.0f), c(0.0f) {}
   // += (dh + dl)(xh + xl), dropping dl*xl
   __device__ __forceinline__ void add(float dh, float dl, float xh, float xl) {
     const float an = __fmaf_rn(dh, xh, A);
     const float d = __fsub_rn(A, an);
     s = __fadd_rn(s, __fmaf_rn(dh, xh, d));
-    s = __fmaf_rn(dh, xl, s);
-    s = __fmaf_rn(dl, xh, s);
+    c = __fmaf_rn(dh, xl, c);
+    c = __fmaf_rn(dl, xh, c);
     A = an;
   }
-  __device__ __forceinline__ dfloat result(float sigma) const { return dfloat{__fsub_rn(A, sigma), s}; }
+  __device__ __forceinline__ dfloat result(float sigma) const {
+    return dfloat{__fsub_rn(A, sigma), __fadd_rn(s, c)};
+  }
 };
+
+// ---- bulk asynchronous copy global -> shared with an mbarrier (Blackwell TMA unit)
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+// bytes: multiple of 16; both addresses 16-byte aligned
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Bounded wait on phase `parity` of an mbarrier: returns false after `limit`
+// polls (each try_wait may itself suspend the thread for a short while).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int limit) {
+  for (int it = 0; it < limit; ++it) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
 
 }  // namespace ceedbp

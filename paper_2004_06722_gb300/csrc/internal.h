@@ -53,11 +53,21 @@ struct SolveState {
   int ncomp;
   int fixed;     // 1: fixed iteration count, never deactivate on tolerance
   int stop;      // 1: every component inactive; kernels return at once
-  int pad;
+  int fault;     // nonzero: a kernel gave up a bounded wait (its results are invalid)
   unsigned int ticket[4];  // last-block counters, one per reduction site
 };
 
-enum TicketSite { kTicketApply = 0, kTicketUpdate = 1, kTicketInit = 2 };
+// Per-problem CG scalars of batched solves.
+struct BatchScalars {
+  CompScalars c;
+  unsigned int ticket[4];
+};
+struct BatchGlobal {
+  int active_count;  // problems still iterating
+  int fault;
+};
+
+enum TicketSite { kTicketApply = 0, kTicketUpdate = 1, kTicketInit = 2, kTicketResidual = 3 };
 
 struct DeviceMesh {
   int p1, q, ncomp, bp;
@@ -67,6 +77,7 @@ struct DeviceMesh {
   const int* off;       // [nglobal+1]; bit 31 of off[g] = Dirichlet flag of node g
   const int* slots;     // [E p1^3] local slots sorted by node, then slot
   const double* basis;  // device 1D tables (layout above)
+  int tune_eb;          // elements per block of the FP32-pair kernel (0 = default; set by the autotuner)
 };
 
 // ---- kernel launchers (one translation unit per family) ----------------------
@@ -109,5 +120,47 @@ cudaError_t launch_pcg_update(const DeviceMesh& m, const double* wl, double* x, 
                               const double* dinv, double* partials, SolveState* st, cudaStream_t s);
 cudaError_t launch_pcg_dir(const DeviceMesh& m, const double* r, double* p, const double* dinv,
                            const SolveState* st, cudaStream_t s);
+
+// FP32-pair path (df.cuh, elem_df.cuh, pcg_df.cu).
+struct dfloat;
+struct ElemDfArgs;
+int elem_df_blocks(const DeviceMesh& m);
+int elem_df_max_tile(const DeviceMesh& m);
+cudaError_t set_df_dconst(int p1, const dfloat* host, cudaStream_t s);
+cudaError_t launch_elem_df(const DeviceMesh& m, const ElemDfArgs& a, cudaStream_t s);
+cudaError_t launch_init_df(const DeviceMesh& m, const double* b, const double* ax, double* x, dfloat* xd, dfloat* r,
+                           dfloat* p, const dfloat* dinv, int x0, double* partials, SolveState* st, double tol,
+                           int fixed, cudaStream_t s);
+cudaError_t launch_update_df(const DeviceMesh& m, const dfloat* wl, dfloat* x, dfloat* r, const dfloat* p,
+                             const dfloat* dinv, double* partials, SolveState* st, cudaStream_t s);
+cudaError_t launch_dir_df(const DeviceMesh& m, const dfloat* r, dfloat* p, const dfloat* dinv, const SolveState* st,
+                          cudaStream_t s);
+cudaError_t launch_df_to_f64(const dfloat* src, double* dst, int64_t n, cudaStream_t s);
+cudaError_t launch_f64_to_df(const double* src, dfloat* dst, int64_t n, cudaStream_t s);
+cudaError_t launch_gs_df(const DeviceMesh& m, const dfloat* wl, double* w, int mask_out, cudaStream_t s);
+
+// Variable coefficient and adjoint gradient (adjoint.cu).
+cudaError_t launch_kappa_grad(const DeviceMesh& m, const double* u, const double* lam, const double* Ghat, double* g,
+                              cudaStream_t s);
+cudaError_t launch_scale_factors(const double* Ghat, const double* kappa, double* G, int64_t nelem, int q3,
+                                 cudaStream_t s);
+cudaError_t launch_misfit(const DeviceMesh& m, const double* mdiag, const double* u, const double* us, double* rhs,
+                          double* partials, unsigned* ticket, double* out, cudaStream_t s);
+
+// Low-precision inner solve of FP64 defect correction (elem_lp.cuh, pcg_lp.cu).
+struct ElemLpArgs;
+int elem_lp_blocks(const DeviceMesh& m);
+cudaError_t launch_elem_lp(const DeviceMesh& m, const ElemLpArgs& a, int bf16, cudaStream_t s);
+cudaError_t launch_residual(const DeviceMesh& m, const double* b, const double* ax, double* r, double* partials,
+                            unsigned* ticket, double* out, cudaStream_t s);
+cudaError_t launch_inner_init(const DeviceMesh& m, int bf16, const double* r64, const double* scale,
+                              const float* dinv, float* x, float* r, void* p, double* partials, SolveState* st,
+                              double tol, cudaStream_t s);
+cudaError_t launch_inner_update(const DeviceMesh& m, int bf16, const float* wl, float* x, float* r, const void* p,
+                                const float* dinv, double* partials, SolveState* st, cudaStream_t s);
+cudaError_t launch_inner_dir(const DeviceMesh& m, int bf16, const float* r, void* p, const float* dinv,
+                             const SolveState* st, cudaStream_t s);
+cudaError_t launch_correct(const DeviceMesh& m, double* x, const float* d, const double* norm, cudaStream_t s);
+cudaError_t launch_narrow(const double* src, void* dst, int64_t n, int bf16, cudaStream_t s);
 
 }  // namespace ceedbp

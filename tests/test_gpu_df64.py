@@ -1,0 +1,115 @@
+"""Parity of the FP64-accurate FP32-pair path (CEEDBP_ARITH_DF64) with the
+CPU FP64 oracle, at the FP64 tolerances: one apply within 1e-12 relative, CG
+iteration counts within 1, final relative residuals within 1e-10."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2004_06722_gb300 as pkg
+from oracle.problems import BakeoffProblem
+from oracle.sampled import sampled_rows
+from synth import box_dims, uniform_pm1
+
+pytestmark = pytest.mark.gpu
+APPLY_TOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    pkg.load_library()
+
+
+def _box(bp, dims, N, arith=pkg.ARITH_DF64, amp=0.05):
+    coords, l2g, dirichlet = pkg.mesh_box(*dims, N, amp)
+    return pkg.Operator(bp, N, coords, l2g, dirichlet, arith=arith)
+
+
+def _vec(n, ncomp, seed):
+    v = uniform_pm1(seed, np.arange(n * ncomp))
+    return v if ncomp == 1 else v.reshape(n, ncomp)
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("bp,N,dims", [(5, 1, (3, 2, 2)), (5, 2, (3, 3, 3)), (5, 3, (3, 2, 5)), (5, 4, (2, 3, 2)),
+                                        (5, 5, (2, 2, 2)), (5, 7, (3, 2, 2)), (5, 8, (2, 1, 2)), (5, 11, (2, 1, 1)),
+                                        (5, 15, (1, 1, 1)), (6, 2, (2, 2, 2)), (6, 3, (3, 2, 2)), (6, 7, (2, 1, 1))])
+def test_df64_apply_parity(bp, N, dims):
+    op = _box(bp, dims, N)
+    ref = BakeoffProblem(bp, *dims, N, amp=0.05)
+    u = _vec(op.nglobal, op.ncomp, 11)
+    w = op.apply(torch.from_numpy(u).cuda()).cpu().numpy()
+    err = _rel(w, ref.apply(u))
+    assert err < APPLY_TOL, err
+
+
+@pytest.mark.parametrize("bp,N,dims", [(5, 3, (3, 2, 2)), (5, 7, (2, 2, 2)), (6, 3, (2, 2, 2)), (5, 2, (4, 3, 3))])
+def test_df64_solve_parity(bp, N, dims):
+    op = _box(bp, dims, N)
+    ref = BakeoffProblem(bp, *dims, N, amp=0.05)
+    b = ref.rhs(_vec(op.nglobal, op.ncomp, 0))
+    x, info = op.solve(torch.from_numpy(np.ascontiguousarray(b)).cuda(), tol=1e-8)
+    x_ref, infos = ref.solve(b, tol=1e-8)
+    for c in range(op.ncomp):
+        assert abs(info["iters"][c] - infos[c]["iters"]) <= 1
+        assert abs(info["rel_res"][c] - infos[c]["rel_res"]) <= 1e-10
+    res = np.linalg.norm(ref.apply(x.cpu().numpy()) - b) / np.linalg.norm(b)
+    assert res < 1e-7
+    assert _rel(x.cpu().numpy(), x_ref) < 1e-6
+
+
+def test_df64_manufactured_4x4x4_n7():
+    op = _box(5, (4, 4, 4), 7)
+    ref = BakeoffProblem(5, 4, 4, 4, 7, amp=0.05)
+    b, u_exact = ref.manufactured_rhs()
+    x, info = op.solve(torch.from_numpy(b).cuda(), tol=1e-8)
+    x_ref, infos = ref.solve(b, tol=1e-8)
+    assert abs(info["iters"][0] - infos[0]["iters"]) <= 1
+    assert abs(info["rel_res"][0] - infos[0]["rel_res"]) <= 1e-10
+    assert abs(np.max(np.abs(x.cpu().numpy() - u_exact)) - np.max(np.abs(x_ref - u_exact))) <= 1e-8
+
+
+def test_df64_matches_fp64_path_and_is_deterministic():
+    dims, N = (4, 4, 3), 7
+    a = _box(5, dims, N)
+    f = _box(5, dims, N, arith=pkg.ARITH_FP64)
+    u = torch.from_numpy(_vec(a.nglobal, 1, 4)).cuda()
+    wa, wf = a.apply(u).clone(), f.apply(u)
+    assert (torch.linalg.norm(wa - wf) / torch.linalg.norm(wf)).item() < 1e-12
+    assert torch.equal(wa, a.apply(u))
+    b = f.mass(u)
+    xa, ia = a.solve(b, fixed_iters=50)
+    xa = xa.clone()
+    xf, i_f = f.solve(b, fixed_iters=50)
+    assert abs(ia["res_norm"][0] - i_f["res_norm"][0]) <= 1e-10 * ia["b_norm"][0]
+    xa2, _ = a.solve(b, fixed_iters=50, chunk=9)
+    assert torch.equal(xa, xa2)
+
+
+def test_df64_x0_restart():
+    op = _box(5, (3, 3, 3), 5)
+    ref = BakeoffProblem(5, 3, 3, 3, 5, amp=0.05)
+    b = torch.from_numpy(ref.rhs(_vec(op.nglobal, 1, 0))).cuda()
+    x, i1 = op.solve(b, fixed_iters=15)
+    x2, i2 = op.solve(b, x=x.clone(), tol=1e-10, x0=True)
+    assert i2["rel_res"][0] <= 1e-10
+    xr, _ = ref.solve(b.cpu().numpy(), tol=1e-12)
+    assert _rel(x2.cpu().numpy(), xr) < 1e-8
+
+
+def test_df64_sampled_rows_largest_n7():
+    dims, N = box_dims(18), 7
+    op = _box(5, dims, N)
+    n = op.nglobal
+    u_h = uniform_pm1(9, np.arange(n))
+    w = op.apply(torch.from_numpy(u_h).cuda())
+    rng = np.random.default_rng(18)
+    nodes = np.unique(np.concatenate([rng.integers(0, n, 24), [0, n - 1, n // 2]]))
+    rows = sampled_rows(5, *dims, N, 0.05, lambda ids: u_h[ids], nodes)
+    got = w[torch.from_numpy(nodes).cuda()].cpu().numpy()
+    assert np.max(np.abs(got - rows)) <= APPLY_TOL * 10 * np.max(np.abs(rows))
+    op.close()

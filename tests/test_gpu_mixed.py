@@ -1,0 +1,52 @@
+"""FP64 defect correction with FP32 and BF16-storage inner solves (BP5, BP6):
+the FP64 residual reaches 1e-10 relative and the solution matches the FP64
+oracle's; the error against the oracle is stated for every case."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2004_06722_gb300 as pkg
+from oracle.problems import BakeoffProblem
+from synth import uniform_pm1
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    pkg.load_library()
+
+
+@pytest.mark.parametrize("bp,N,dims", [(5, 7, (3, 2, 2)), (6, 3, (3, 3, 2)), (6, 7, (2, 2, 2)), (5, 3, (4, 4, 4))])
+@pytest.mark.parametrize("mixed", [pkg.MIXED_FP32, pkg.MIXED_BF16])
+@pytest.mark.parametrize("arith", [pkg.ARITH_FP64, pkg.ARITH_DF64])
+def test_defect_correction_reaches_fp64_tolerance(bp, N, dims, mixed, arith):
+    coords, l2g, dirichlet = pkg.mesh_box(*dims, N, 0.05)
+    op = pkg.Operator(bp, N, coords, l2g, dirichlet, arith=arith)
+    op.prepare_mixed(mixed)
+    ref = BakeoffProblem(bp, *dims, N, amp=0.05)
+    nc = op.ncomp
+    r = uniform_pm1(0, np.arange(op.nglobal * nc))
+    b = ref.rhs(r if nc == 1 else r.reshape(-1, 3))
+    bt = torch.from_numpy(np.ascontiguousarray(b)).cuda()
+    x, info = op.solve(bt, tol=1e-10, mixed=mixed)
+    assert info["status"] == "OK" and info["outer_iters"] >= 1
+    assert max(info["rel_res"]) <= 1e-10
+    xh = x.cpu().numpy()
+    res = np.linalg.norm(ref.apply(xh) - b) / np.linalg.norm(b)
+    assert res <= 2e-10, res
+    x_ref, _ = ref.solve(b, tol=1e-13)
+    err = np.linalg.norm(xh - x_ref) / np.linalg.norm(x_ref)
+    print(f"bp{bp} N={N} mixed={mixed} arith={arith}: outer {info['outer_iters']}, inner {info['iters']}, "
+          f"|x - x_oracle|/|x_oracle| = {err:.2e}")
+    assert err <= 1e-7
+
+
+def test_mixed_requires_prepare():
+    op = pkg.Operator.box(5, 2, 2, 2, 3)
+    b = torch.ones(op.nglobal, dtype=torch.float64, device="cuda")
+    with pytest.raises(pkg.CeedbpError) as ei:
+        op.solve(b, mixed=pkg.MIXED_FP32)
+    assert ei.value.status == pkg.EINVAL
