@@ -41,7 +41,8 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--order", type=int, default=7)
     ap.add_argument("--arith", choices=["fp64", "df64"], default="fp64",
-                    help="fp64: native FP64 instructions; df64: FP64-accurate FP32 pairs")
+                    help="headline arithmetic: fp64 native FP64 instructions; df64 FP64-accurate FP32 pairs")
+    ap.add_argument("--headline-only", action="store_true", help="skip the other arithmetic variant")
     ap.add_argument("--k", type=int, default=18, help="E = 2^k elements (N=7: k=18 is n = 8.99e7)")
     ap.add_argument("--no-sweep", action="store_true", help="skip the n sweep (r_max, n_0.8, t_0.8)")
     ap.add_argument("--sweep-iters", type=int, default=100)
@@ -154,48 +155,39 @@ def n_08(ns, rates):
     return float(ns[-1])
 
 
-def make_problem(pkg, N, k, seed, device, arith=0):
+def make_mesh(pkg, N, k):
+    from synth import box_dims
+    dims = box_dims(k)
+    coords, l2g, dirichlet = pkg.mesh_box(*dims, N, 0.05)
+    return dims, coords, l2g, dirichlet
+
+
+def make_problem(pkg, N, mesh, seed, device, arith=0):
     import numpy as np
     import torch
 
-    from synth import box_dims, uniform_pm1
-    dims = box_dims(k)
-    coords, l2g, dirichlet = pkg.mesh_box(*dims, N, 0.05)
+    from synth import uniform_pm1
+    dims, coords, l2g, dirichlet = mesh
     op = pkg.Operator(5, N, coords, l2g, dirichlet, device=device, arith=arith)
-    del coords, l2g
     r = torch.from_numpy(uniform_pm1(seed, np.arange(op.nglobal))).to(device)
     mask = torch.from_numpy(1.0 - dirichlet.astype(np.float64)).to(device)
     b = op.mass(r) * mask
     E = dims[0] * dims[1] * dims[2]
-    return op, b, E * N ** 3, dims
+    return op, b, E * N ** 3
 
 
-def run_ours(args):
-    import numpy as np
+def measure(pkg, args, mesh, arith, device, rank, world, dist):
+    """One arithmetic variant at the headline size: timed graph, per-kernel profile, end-to-end."""
     import torch
-    import torch.distributed as dist
-
-    import paper_2004_06722_gb300 as pkg
-
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    device = torch.device("cuda", local)
     N, K, W = args.order, args.steps, max(3, args.warmup)
-
-    arith = pkg.ARITH_DF64 if args.arith == "df64" else pkg.ARITH_FP64
-    op, b, n_dofs, dims = make_problem(pkg, N, args.k, seed=rank, device=device, arith=arith)
+    op, b, n_dofs = make_problem(pkg, N, mesh, seed=rank, device=device, arith=arith)
+    dims = mesh[0]
     x = op.empty()
-    # warm-up: graph capture for the timed chunk length, plus W iterations
-    op.solve(b, x, fixed_iters=K, chunk=K)
+    op.solve(b, x, fixed_iters=K, chunk=K)  # graph capture for the timed chunk length
     op.solve(b, x, fixed_iters=W, chunk=W)
     torch.cuda.synchronize()
-
     vis = os.environ.get("CUDA_VISIBLE_DEVICES")
-    clocks = Clocks(vis.split(",")[local] if vis else str(local))
+    clocks = Clocks(vis.split(",")[device.index] if vis else str(device.index))
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -213,11 +205,9 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     value = world * n_dofs * K / (ms * 1e-3)
-
     # per-kernel durations: the same K-iteration graph with event-record nodes around each kernel
     _, pinfo = op.solve(b, x, fixed_iters=K, chunk=K, profile=True)
     elem_ms = pinfo["kernel_ms"][0]
-
     # end to end through the public API: pinned host RHS in, solution back to pinned host memory
     b_h = b.cpu().pin_memory()
     x_h = torch.empty_like(b_h).pin_memory()
@@ -238,10 +228,9 @@ def run_ours(args):
     fp64_tf, fp64_src = fp64_peak_tflops(peaks)
     elem_flops = elem_flops_dof * n_dofs
     elem_bytes = elem_bytes_dof * n_dofs
-    t_flop = elem_flops / (fp64_tf * 1e12)
-    t_byte = elem_bytes / (peaks["hbm_gbs"] * 1e9)
-    traffic = ncu_traffic(f"bk5_{args.arith}_n{N}.md")
-    if t_flop >= t_byte and args.arith == "fp64":
+    name = "fp64" if arith == pkg.ARITH_FP64 else "df64"
+    traffic = ncu_traffic(f"bk5_{name}_n{N}.md")
+    if arith == pkg.ARITH_FP64:
         ach = elem_flops / (elem_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": fp64_tf, "unit": "TFLOP/s", "frac": ach / fp64_tf,
                 "traffic": traffic, "kernel": "elem_kernel (BK5, FP64)", "peak_source": fp64_src,
@@ -250,23 +239,13 @@ def run_ours(args):
         ach = elem_bytes / (elem_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / peaks["hbm_gbs"], "traffic": traffic,
-                "kernel": "elem_df_kernel (BK5, FP64-accurate FP32 pairs)" if args.arith == "df64"
-                else "elem_kernel (BK5, FP64)",
-                "peak_source": f"{peak_src} hbm_gbs",
+                "kernel": "elem_df_kernel (BK5, FP64-accurate FP32 pairs)", "peak_source": f"{peak_src} hbm_gbs",
                 "fp64_equiv_tflops": elem_flops / (elem_ms * 1e-3) / 1e12}
     roof.update({"elem_ms": elem_ms, "update_ms": pinfo["kernel_ms"][1], "dir_ms": pinfo["kernel_ms"][2],
                  "algorithmic_bytes_per_dof": elem_bytes_dof, "flops_per_dof": elem_flops_dof})
-
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
-        "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.arith == "fp64" else "df64 (FP32 pairs, FP64-accurate)", "data": "synthetic",
-        "config": {"workload": f"BP5 FP64 Jacobi-PCG, N={N}, E={dims[0]}x{dims[1]}x{dims[2]}={dims[0]*dims[1]*dims[2]} "
-                               f"deformed box (amp 0.05), n=E*N^3={n_dofs}, RHS B*r with r seeded U[-1,1]",
-                   "n": n_dofs, "order": N, "elements": list(dims), "nglobal": op.nglobal,
-                   "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 "
-                   f"(geometric factors {6 * 8 * (N + 1) ** 3 * dims[0] * dims[1] * dims[2] / 1e9:.1f} GB per iteration)",
-                   "timing": "CUDA events around one captured graph of K iterations on the solver stream"},
+    out = {
+        "value": value, "ms_per_step": ms / K,
+        "dtype": "f64" if arith == pkg.ARITH_FP64 else "df64 (FP32 pairs, FP64-accurate)",
         "hbm_roofline": {"bytes_per_dof_iter": iter_bytes_dof,
                          "roofline_dofs_per_s": peaks["hbm_gbs"] * 1e9 / iter_bytes_dof,
                          "frac": value / world / (peaks["hbm_gbs"] * 1e9 / iter_bytes_dof)},
@@ -278,12 +257,53 @@ def run_ours(args):
         "clocks": clk,
         "wall_s_timed": wall,
         "solver": {"rel_res_after_K": info["rel_res"][0], "status": info["status"]},
+        "n": n_dofs, "nglobal": op.nglobal, "elements": list(dims),
     }
     op.close()
-    del b, x
+    return out
 
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2004_06722_gb300 as pkg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    N, K, W = args.order, args.steps, max(3, args.warmup)
+    mesh = make_mesh(pkg, N, args.k)
+    head_arith = pkg.ARITH_DF64 if args.arith == "df64" else pkg.ARITH_FP64
+    head = measure(pkg, args, mesh, head_arith, device, rank, world, dist)
+    variants = {}
+    if not args.headline_only:
+        other = pkg.ARITH_FP64 if head_arith == pkg.ARITH_DF64 else pkg.ARITH_DF64
+        variants["df64" if other == pkg.ARITH_DF64 else "fp64"] = measure(pkg, args, mesh, other, device, rank,
+                                                                           world, dist)
+    dims, n_dofs = head["elements"], head["n"]
+    line = {
+        "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": head["dtype"], "data": "synthetic",
+        "config": {"workload": f"BP5 Jacobi-PCG, N={N}, E={dims[0]}x{dims[1]}x{dims[2]}={dims[0]*dims[1]*dims[2]} "
+                               f"deformed box (amp 0.05), n=E*N^3={n_dofs}, RHS B*r with r seeded U[-1,1]",
+                   "n": n_dofs, "order": N, "elements": dims, "nglobal": head["nglobal"],
+                   "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 "
+                   f"(geometric factors {6 * 8 * (N + 1) ** 3 * dims[0] * dims[1] * dims[2] / 1e9:.1f} GB per iteration)",
+                   "timing": "CUDA events around one captured graph of K iterations on the solver stream"},
+        "hbm_roofline": head["hbm_roofline"], "roofline": head["roofline"], "e2e": head["e2e"],
+        "gpu_launches": head["gpu_launches"], "clocks": head["clocks"], "wall_s_timed": head["wall_s_timed"],
+        "solver": head["solver"], "variants": variants,
+    }
+    del mesh
     if not args.no_sweep and rank == 0:
-        line["sweep"] = run_sweep(pkg, N, args.sweep_iters, device, arith)
+        line["sweep"] = run_sweep(pkg, N, args.sweep_iters, device, [head_arith] + (
+            [] if args.headline_only else [pkg.ARITH_DF64 if head_arith == pkg.ARITH_FP64 else pkg.ARITH_FP64]))
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         line["cpu_baseline"] = cpu_baseline(N, args.cpu_sample_k, iters=20)
     if world > 1:
@@ -293,29 +313,35 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
 
 
-def run_sweep(pkg, N, iters, device, arith=0):
+def run_sweep(pkg, N, iters, device, ariths):
     import torch
 
     from synth import sweep_ks
-    ns, rates, ms_iter = [], [], []
+    res = {a: {"n": [], "dofs_per_s": [], "ms_per_iter": []} for a in ariths}
     for k in sweep_ks(N):
-        op, b, n_dofs, dims = make_problem(pkg, N, k, seed=0, device=device, arith=arith)
-        x = op.empty()
-        op.solve(b, x, fixed_iters=iters, chunk=iters)
-        best = None
-        for _ in range(3):
-            _, info = op.solve(b, x, fixed_iters=iters, chunk=iters)
-            best = info["device_ms"] if best is None else min(best, info["device_ms"])
-        ns.append(n_dofs)
-        rates.append(n_dofs * iters / (best * 1e-3))
-        ms_iter.append(best / iters)
-        op.close()
-        del b, x
+        mesh = make_mesh(pkg, N, k)
+        for a in ariths:
+            op, b, n_dofs = make_problem(pkg, N, mesh, seed=0, device=device, arith=a)
+            x = op.empty()
+            op.solve(b, x, fixed_iters=iters, chunk=iters)
+            best = None
+            for _ in range(3):
+                _, info = op.solve(b, x, fixed_iters=iters, chunk=iters)
+                best = info["device_ms"] if best is None else min(best, info["device_ms"])
+            res[a]["n"].append(n_dofs)
+            res[a]["dofs_per_s"].append(n_dofs * iters / (best * 1e-3))
+            res[a]["ms_per_iter"].append(best / iters)
+            op.close()
+            del b, x
+        del mesh
         torch.cuda.empty_cache()
-    rmax = max(rates)
-    n80 = n_08(ns, rates)
-    return {"order": N, "iters": iters, "n": ns, "dofs_per_s": rates, "ms_per_iter": ms_iter,
-            "r_max": rmax, "n_0.8": n80, "t_0.8_s": 1.25 * n80 / rmax}
+    out = {}
+    for a, r in res.items():
+        rmax = max(r["dofs_per_s"])
+        n80 = n_08(r["n"], r["dofs_per_s"])
+        out["fp64" if a == pkg.ARITH_FP64 else "df64"] = dict(
+            r, order=N, iters=iters, r_max=rmax, **{"n_0.8": n80, "t_0.8_s": 1.25 * n80 / rmax})
+    return out
 
 
 def cpu_baseline(N, k, iters):

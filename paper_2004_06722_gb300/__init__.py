@@ -137,7 +137,13 @@ class Operator:
         coords = np.ascontiguousarray(coords, dtype=np.float64)
         l2g = np.ascontiguousarray(l2g, dtype=np.int64)
         self.nelem = coords.shape[0]
+        p1 = order + 1
+        if coords.shape != (self.nelem, p1 ** 3, 3) or l2g.shape != (self.nelem, p1 ** 3):
+            raise ValueError(f"coords must be [E, {p1 ** 3}, 3] and l2g [E, {p1 ** 3}] for order {order}")
         self.nglobal = int(dirichlet.shape[0]) if dirichlet is not None else int(l2g.max()) + 1
+        q = order + 1 if bp in (5, 6) else order + 2
+        if kappa is not None and np.asarray(kappa).size != self.nelem * q ** 3:
+            raise ValueError(f"kappa must hold E * {q ** 3} values")
         dirichlet = None if dirichlet is None else np.ascontiguousarray(dirichlet, dtype=np.uint8)
         kappa = None if kappa is None else np.ascontiguousarray(kappa, dtype=np.float64)
         self.arith = arith

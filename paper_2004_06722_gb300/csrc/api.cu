@@ -275,31 +275,32 @@ ceedbp_status setup_impl(ceedbp_ctx* c, const double* coords, const int64_t* l2g
     a.dnorm_col = c->dnorm_col;
     a.mask_in = 1;
     a.fault = &c->d_state->fault;
-    CK(c, launch_elem_df(m, a, s));
     CK(c, cudaStreamSynchronize(s));
-    // autotuner: elements per block of the pair kernel, timed on this mesh
-    const int max_eb = elem_df_max_tile(m);
-    if (max_eb > 1) {
-      float best = 1e30f;
-      int best_eb = 1;
-      for (int eb = 1; eb <= max_eb; ++eb) {
-        m.tune_eb = eb;
-        CK(c, launch_elem_df(m, a, s));  // warm-up of this shape
-        CK(c, cudaEventRecord(c->ev0, s));
-        for (int r = 0; r < 3; ++r) CK(c, launch_elem_df(m, a, s));
-        CK(c, cudaEventRecord(c->ev1, s));
-        CK(c, cudaEventSynchronize(c->ev1));
-        float ms = 0.0f;
-        CK(c, cudaEventElapsedTime(&ms, c->ev0, c->ev1));
-        if (ms < best) {
-          best = ms;
-          best_eb = eb;
-        }
+    // autotuner: elements per block and G staging of the pair kernel, timed on this mesh
+    int cand_eb[16], cand_st[16];
+    const int ncand = elem_df_tile_candidates(m, cand_eb, cand_st, 16);
+    if (ncand == 0) return fail(c, CEEDBP_EUNSUPPORTED, "no launchable shape for the pair kernel at this order");
+    float best = 1e30f;
+    int best_k = 0;
+    for (int k = 0; k < ncand && ncand > 1; ++k) {
+      m.tune_eb = cand_eb[k];
+      m.tune_stage = cand_st[k];
+      CK(c, launch_elem_df(m, a, s));  // warm-up of this shape
+      CK(c, cudaEventRecord(c->ev0, s));
+      for (int r = 0; r < 3; ++r) CK(c, launch_elem_df(m, a, s));
+      CK(c, cudaEventRecord(c->ev1, s));
+      CK(c, cudaEventSynchronize(c->ev1));
+      float ms = 0.0f;
+      CK(c, cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+      if (ms < best) {
+        best = ms;
+        best_k = k;
       }
-      m.tune_eb = best_eb;
-    } else {
-      m.tune_eb = 1;
     }
+    m.tune_eb = cand_eb[best_k];
+    m.tune_stage = cand_st[best_k];
+    CK(c, launch_elem_df(m, a, s));  // the chosen shape, launched once outside any capture
+    CK(c, cudaStreamSynchronize(s));
     CK(c, cudaMemsetAsync(&c->d_state->fault, 0, sizeof(int), s));
   }
   CK(c, cudaStreamSynchronize(s));

@@ -27,7 +27,7 @@ namespace ceedbp {
 // included by the one translation unit that instantiates the kernels.
 __constant__ dfloat c_Ddf[kMaxP1 - 1][kMaxP1 * kMaxP1];
 
-template <int P1, int NC>
+template <int P1, int NC, bool STAGE>
 struct ElemDfShape {
   static constexpr int PP = P1 * P1, P3 = PP * P1;
   static constexpr int ROW = P1 + 1;            // padded row length (pairs)
@@ -35,7 +35,7 @@ struct ElemDfShape {
   static constexpr int TILE = P1 * SLAB;        // padded tile (pairs)
   // G of an element (6 p1^3 pairs, contiguous in memory) is staged in shared
   // memory by one bulk asynchronous copy when it fits next to the tiles.
-  static constexpr bool STAGE_G = P1 <= 10;
+  static constexpr bool STAGE_G = STAGE && P1 <= 10;
   static constexpr int GSTAGE = STAGE_G ? 6 * P3 : 0;  // pairs per element
 };
 
@@ -47,24 +47,24 @@ inline int elem_df_per_block() {
 
 // layout: [mbarrier 16 B][red 32 NC doubles][smax 128 u32][sD p1 x (p1+1) pairs, padded to 16 B]
 //         then per element: [G stage][sX][sR][sS]
-template <int P1, int NC>
+template <int P1, int NC, bool STAGE>
 __host__ __device__ inline size_t elem_df_head_bytes() {
-  using S = ElemDfShape<P1, NC>;
+  using S = ElemDfShape<P1, NC, STAGE>;
   const size_t h = 16 + sizeof(double) * 32 * NC + sizeof(unsigned) * 128 + sizeof(dfloat) * P1 * S::ROW;
   return (h + 15) / 16 * 16;
 }
 
-template <int P1, int NC>
+template <int P1, int NC, bool STAGE>
 __host__ __device__ inline size_t elem_df_slot_pairs() {
-  using S = ElemDfShape<P1, NC>;
+  using S = ElemDfShape<P1, NC, STAGE>;
   return size_t(S::GSTAGE) + 3 * NC * S::TILE + 1;  // +1 pair keeps every slot 16-byte aligned
 }
 
-template <int P1, int NC>
+template <int P1, int NC, bool STAGE>
 inline size_t elem_df_smem_bytes(int eb) {
-  size_t slot = elem_df_slot_pairs<P1, NC>();
+  size_t slot = elem_df_slot_pairs<P1, NC, STAGE>();
   slot = (slot + 1) / 2 * 2;
-  return elem_df_head_bytes<P1, NC>() + sizeof(dfloat) * size_t(eb) * slot;
+  return elem_df_head_bytes<P1, NC, STAGE>() + sizeof(dfloat) * size_t(eb) * slot;
 }
 
 __device__ __forceinline__ float row_abs_sum3(dfloat a, dfloat b, dfloat c) {
@@ -84,9 +84,9 @@ __device__ __forceinline__ void slot_max(unsigned* dst, float v, bool active) {
 
 constexpr int kMbarPolls = 1 << 22;
 
-template <int P1, int NC>
+template <int P1, int NC, bool STAGE>
 __global__ void elem_df_kernel(const DeviceMesh m, const ElemDfArgs a, const int eb) {
-  using S = ElemDfShape<P1, NC>;
+  using S = ElemDfShape<P1, NC, STAGE>;
   constexpr int PP = S::PP, P3 = S::P3, ROW = S::ROW, SLAB = S::SLAB, TILE = S::TILE;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (a.state != nullptr && a.state->stop) return;
@@ -95,8 +95,8 @@ __global__ void elem_df_kernel(const DeviceMesh m, const ElemDfArgs a, const int
   double* red = reinterpret_cast<double*>(smem_raw + 16);                 // 32 * NC
   unsigned* smax = reinterpret_cast<unsigned*>(red + 32 * NC);            // [4][32]
   dfloat* sD = reinterpret_cast<dfloat*>(smax + 128);                     // [P1][ROW]
-  dfloat* ebuf = reinterpret_cast<dfloat*>(smem_raw + elem_df_head_bytes<P1, NC>());
-  size_t slot_pairs = elem_df_slot_pairs<P1, NC>();
+  dfloat* ebuf = reinterpret_cast<dfloat*>(smem_raw + elem_df_head_bytes<P1, NC, STAGE>());
+  size_t slot_pairs = elem_df_slot_pairs<P1, NC, STAGE>();
   slot_pairs = (slot_pairs + 1) / 2 * 2;
 
   const int tid = threadIdx.x;
@@ -184,6 +184,14 @@ __global__ void elem_df_kernel(const DeviceMesh m, const ElemDfArgs a, const int
       Dj[n] = sD[j * ROW + n];
     }
     const dfloat* Gg = a.G + size_t(e) * 6 * P3;
+    dfloat gnext[6];
+    if constexpr (!S::STAGE_G) {
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        const float2 v = __ldcs(reinterpret_cast<const float2*>(Gg + q * P3 + t));
+        gnext[q] = dfloat{v.x, v.y};
+      }
+    }
 #pragma unroll
     for (int k = 0; k < P1; ++k) {
       const int pt = k * PP + t;
@@ -193,8 +201,11 @@ __global__ void elem_df_kernel(const DeviceMesh m, const ElemDfArgs a, const int
         if constexpr (S::STAGE_G) {
           g[q] = sG[q * P3 + pt];
         } else {
-          const float2 v = __ldcs(reinterpret_cast<const float2*>(Gg + q * P3 + pt));
-          g[q] = dfloat{v.x, v.y};
+          g[q] = gnext[q];
+          if (k + 1 < P1) {  // next slab in flight while this one is used
+            const float2 v = __ldcs(reinterpret_cast<const float2*>(Gg + q * P3 + pt + PP));
+            gnext[q] = dfloat{v.x, v.y};
+          }
         }
       }
       const float gb = fmaxf(fmaxf(row_abs_sum3(g[0], g[1], g[2]), row_abs_sum3(g[1], g[3], g[4])),
@@ -349,41 +360,79 @@ __global__ void elem_df_kernel(const DeviceMesh m, const ElemDfArgs a, const int
 
 constexpr size_t kMaxSmemPerBlock = 220 * 1024;  // below the 227 KB opt-in limit with room for static shared memory
 
-// elements per block: the tuned value when set, else the default, reduced until
-// the shared memory fits
-template <int P1, int NC>
-inline int elem_df_eb(const DeviceMesh& m) {
-  int eb = m.tune_eb > 0 ? m.tune_eb : elem_df_per_block<P1, NC>();
-  while (eb > 1 && elem_df_smem_bytes<P1, NC>(eb) > kMaxSmemPerBlock) --eb;
-  return eb;
+template <int P1, int NC, bool STAGE>
+cudaError_t elem_df_attr() {
+  static const cudaError_t attr = cudaFuncSetAttribute(elem_df_kernel<P1, NC, STAGE>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       int(kMaxSmemPerBlock));
+  return attr;
 }
 
+// elements per block: the tuned value when set, else the default
 template <int P1, int NC>
-inline int elem_df_max_eb() {
-  int eb = 1;
-  while (eb < 8 && elem_df_smem_bytes<P1, NC>(eb + 1) <= kMaxSmemPerBlock && (eb + 1) * P1 * P1 <= 1024) ++eb;
-  return eb;
+inline int elem_df_eb(const DeviceMesh& m) {
+  return m.tune_eb > 0 ? m.tune_eb : elem_df_per_block<P1, NC>();
+}
+
+// Whether a shape (elements per block, staging) can run: shared memory within
+// the limit and at least one block resident per SM (registers included).
+template <int P1, int NC, bool STAGE>
+inline bool elem_df_shape_ok(int eb) {
+  const size_t smem = elem_df_smem_bytes<P1, NC, STAGE>(eb);
+  const int nthreads = ((eb * P1 * P1 + 31) / 32) * 32;
+  if (smem > kMaxSmemPerBlock || nthreads > 1024) return false;
+  if (elem_df_attr<P1, NC, STAGE>() != cudaSuccess) return false;
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, elem_df_kernel<P1, NC, STAGE>, nthreads, smem) !=
+      cudaSuccess)
+    return false;
+  return nb >= 1;
+}
+
+template <int P1, int NC, bool STAGE>
+cudaError_t launch_elem_df_s(const DeviceMesh& m, const ElemDfArgs& a, cudaStream_t s) {
+  const int eb = elem_df_eb<P1, NC>(m);
+  const int nthreads = ((eb * P1 * P1 + 31) / 32) * 32;
+  const size_t smem = elem_df_smem_bytes<P1, NC, STAGE>(eb);
+  if (smem > kMaxSmemPerBlock) return cudaErrorInvalidConfiguration;
+  const cudaError_t attr = elem_df_attr<P1, NC, STAGE>();
+  if (attr != cudaSuccess) return attr;
+  const int64_t blocks = a.blk_prob != nullptr ? int64_t(a.batch_blocks) : (m.nelem + eb - 1) / eb;
+  elem_df_kernel<P1, NC, STAGE><<<unsigned(blocks), nthreads, smem, s>>>(m, a, eb);
+  return cudaGetLastError();
 }
 
 template <int P1, int NC>
 cudaError_t launch_elem_df_t(const DeviceMesh& m, const ElemDfArgs& a, cudaStream_t s) {
-  const int eb = elem_df_eb<P1, NC>(m);
-  const int nthreads = ((eb * P1 * P1 + 31) / 32) * 32;
-  const size_t smem = elem_df_smem_bytes<P1, NC>(eb);
-  if (smem > kMaxSmemPerBlock) return cudaErrorInvalidConfiguration;
-  auto kern = elem_df_kernel<P1, NC>;
-  static const cudaError_t attr =
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kMaxSmemPerBlock));
-  if (attr != cudaSuccess) return attr;
-  const int64_t blocks = a.blk_prob != nullptr ? int64_t(a.batch_blocks) : (m.nelem + eb - 1) / eb;
-  kern<<<unsigned(blocks), nthreads, smem, s>>>(m, a, eb);
-  return cudaGetLastError();
+  if constexpr (P1 <= 10) {
+    if (m.tune_stage) return launch_elem_df_s<P1, NC, true>(m, a, s);
+  }
+  return launch_elem_df_s<P1, NC, false>(m, a, s);
 }
 
 template <int P1, int NC>
 inline int elem_df_blocks_t(const DeviceMesh& m) {
   const int eb = elem_df_eb<P1, NC>(m);
   return int((m.nelem + eb - 1) / eb);
+}
+
+// candidate shapes for the autotuner: (elements per block, staged) pairs that can run
+template <int P1, int NC>
+inline int elem_df_candidates(int* eb_out, int* stage_out, int cap) {
+  int n = 0;
+  for (int eb = 1; eb <= 4 && n < cap; ++eb) {
+    if (elem_df_shape_ok<P1, NC, false>(eb)) {
+      eb_out[n] = eb;
+      stage_out[n++] = 0;
+    }
+    if constexpr (P1 <= 10) {
+      if (n < cap && elem_df_shape_ok<P1, NC, true>(eb)) {
+        eb_out[n] = eb;
+        stage_out[n++] = 1;
+      }
+    }
+  }
+  return n;
 }
 
 }  // namespace ceedbp

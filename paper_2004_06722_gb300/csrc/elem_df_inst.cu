@@ -15,9 +15,9 @@ cudaError_t set_df_dconst(int p1, const dfloat* host, cudaStream_t s) {
 #define CEEDBP_DF_BLOCKS(P) \
   case P:                   \
     return m.ncomp == 3 ? elem_df_blocks_t<P, 3>(m) : elem_df_blocks_t<P, 1>(m);
-#define CEEDBP_DF_MAXEB(P) \
-  case P:                  \
-    return m.ncomp == 3 ? elem_df_max_eb<P, 3>() : elem_df_max_eb<P, 1>();
+#define CEEDBP_DF_CAND(P) \
+  case P:                 \
+    return m.ncomp == 3 ? elem_df_candidates<P, 3>(eb, stage, cap) : elem_df_candidates<P, 1>(eb, stage, cap);
 
 cudaError_t launch_elem_df(const DeviceMesh& m, const ElemDfArgs& a, cudaStream_t s) {
   switch (m.p1) {
@@ -37,12 +37,12 @@ int elem_df_blocks(const DeviceMesh& m) {
   }
 }
 
-int elem_df_max_tile(const DeviceMesh& m) {
+int elem_df_tile_candidates(const DeviceMesh& m, int* eb, int* stage, int cap) {
   switch (m.p1) {
-    CEEDBP_DF_MAXEB(2) CEEDBP_DF_MAXEB(3) CEEDBP_DF_MAXEB(4) CEEDBP_DF_MAXEB(5) CEEDBP_DF_MAXEB(6)
-    CEEDBP_DF_MAXEB(7) CEEDBP_DF_MAXEB(8) CEEDBP_DF_MAXEB(9) CEEDBP_DF_MAXEB(10) CEEDBP_DF_MAXEB(11)
-    CEEDBP_DF_MAXEB(12) CEEDBP_DF_MAXEB(13) CEEDBP_DF_MAXEB(14) CEEDBP_DF_MAXEB(15) CEEDBP_DF_MAXEB(16)
-    default: return 1;
+    CEEDBP_DF_CAND(2) CEEDBP_DF_CAND(3) CEEDBP_DF_CAND(4) CEEDBP_DF_CAND(5) CEEDBP_DF_CAND(6)
+    CEEDBP_DF_CAND(7) CEEDBP_DF_CAND(8) CEEDBP_DF_CAND(9) CEEDBP_DF_CAND(10) CEEDBP_DF_CAND(11)
+    CEEDBP_DF_CAND(12) CEEDBP_DF_CAND(13) CEEDBP_DF_CAND(14) CEEDBP_DF_CAND(15) CEEDBP_DF_CAND(16)
+    default: return 0;
   }
 }
 

@@ -78,6 +78,7 @@ struct DeviceMesh {
   const int* slots;     // [E p1^3] local slots sorted by node, then slot
   const double* basis;  // device 1D tables (layout above)
   int tune_eb;          // elements per block of the FP32-pair kernel (0 = default; set by the autotuner)
+  int tune_stage;       // 1: stage G in shared memory with a bulk copy (autotuner), 0: register prefetch
 };
 
 // ---- kernel launchers (one translation unit per family) ----------------------
@@ -125,7 +126,7 @@ cudaError_t launch_pcg_dir(const DeviceMesh& m, const double* r, double* p, cons
 struct dfloat;
 struct ElemDfArgs;
 int elem_df_blocks(const DeviceMesh& m);
-int elem_df_max_tile(const DeviceMesh& m);
+int elem_df_tile_candidates(const DeviceMesh& m, int* eb, int* stage, int cap);
 cudaError_t set_df_dconst(int p1, const dfloat* host, cudaStream_t s);
 cudaError_t launch_elem_df(const DeviceMesh& m, const ElemDfArgs& a, cudaStream_t s);
 cudaError_t launch_init_df(const DeviceMesh& m, const double* b, const double* ax, double* x, dfloat* xd, dfloat* r,
