@@ -259,6 +259,9 @@ def measure(pkg, args, mesh, arith, device, rank, world, dist):
         "solver": {"rel_res_after_K": info["rel_res"][0], "status": info["status"]},
         "n": n_dofs, "nglobal": op.nglobal, "elements": list(dims),
     }
+    if arith != pkg.ARITH_FP64:
+        eb, staged = op.tile_info()
+        out["roofline"]["tile"] = {"elements_per_block": eb, "g_staged_by_bulk_copy": bool(staged)}
     op.close()
     return out
 

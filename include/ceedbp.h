@@ -261,6 +261,12 @@ ceedbp_status ceedbp_batch_solve(ceedbp_batch* batch, const double* const* b_dev
 ceedbp_status ceedbp_batch_destroy(ceedbp_batch* batch);
 const char* ceedbp_batch_last_error(const ceedbp_batch* batch);
 
+/* Shape the setup autotuner chose for the FP32-pair element kernel
+ * (CEEDBP_ARITH_DF64): elements per thread block and whether G is staged in
+ * shared memory by a bulk asynchronous copy (1) or prefetched into registers (0).
+ * Both outputs are 0 for contexts without the pair path. */
+ceedbp_status ceedbp_tile_info(const ceedbp_ctx* ctx, int* elems_per_block, int* staged);
+
 /* Release every resource owned by ctx (NULL is accepted). */
 ceedbp_status ceedbp_destroy(ceedbp_ctx* ctx);
 

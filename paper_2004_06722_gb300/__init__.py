@@ -68,6 +68,7 @@ _SIGS = {
     "ceedbp_solve": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo)]),
     "ceedbp_apply_noalloc": (ctypes.c_int, [_P, _P, _P, _P]),
     "ceedbp_destroy": (ctypes.c_int, [_P]),
+    "ceedbp_tile_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "ceedbp_batch_setup": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(Params), ctypes.POINTER(_P),
                                           ctypes.POINTER(_P), ctypes.POINTER(_P), _P, ctypes.POINTER(_P)]),
     "ceedbp_batch_solve": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(SolveOpts),
@@ -252,6 +253,12 @@ class Operator:
         _check(self._call(self.lib.ceedbp_kappa_gradient, self._vec(u), self._vec(lam),
                           self._ptr_t(g, self.nelem * self.nquad ** 3)), self.ctx)
         return g
+
+    def tile_info(self):
+        """(elements per block, G staged) chosen by the setup autotuner for the pair kernel."""
+        eb, st = ctypes.c_int(0), ctypes.c_int(0)
+        _check(self.lib.ceedbp_tile_info(self.ctx, ctypes.byref(eb), ctypes.byref(st)), self.ctx)
+        return eb.value, st.value
 
     def prepare_mixed(self, precision: int):
         _check(self._call(self.lib.ceedbp_prepare_mixed, precision), self.ctx)

@@ -21,7 +21,16 @@ int elem_blocks_bp3(const DeviceMesh& m);
 int elem_blocks_bp5(const DeviceMesh& m);
 int elem_blocks_bp6(const DeviceMesh& m);
 
+cudaError_t launch_elem_eo(const DeviceMesh& m, const ElemArgs& a, cudaStream_t s);
+int elem_eo_blocks(const DeviceMesh& m);
+bool elem_eo_available(const DeviceMesh& m);
+
+// Collocated FP64 stiffness with even p1 (odd order) uses the even-odd kernel
+// when its shape is resident on an SM (large p1 with three components is not).
+static bool use_even_odd(const DeviceMesh& m) { return m.colloc && (m.p1 % 2 == 0) && elem_eo_available(m); }
+
 cudaError_t launch_elem(const DeviceMesh& m, int kind, const ElemArgs& a, cudaStream_t s) {
+  if (kind == kStiff && use_even_odd(m)) return launch_elem_eo(m, a, s);
   if (m.colloc && kind == kStiff) return m.ncomp == 3 ? launch_elem_bp6(m, a, s) : launch_elem_bp5(m, a, s);
   if (!m.colloc && kind == kStiff && m.ncomp == 1) return launch_elem_bp3(m, a, s);
   if (!m.colloc && kind == kMass && m.ncomp == 1) return launch_elem_bp1(m, a, s);
@@ -30,6 +39,7 @@ cudaError_t launch_elem(const DeviceMesh& m, int kind, const ElemArgs& a, cudaSt
 
 int elem_blocks(const DeviceMesh& m) {
   // stiffness and mass instantiations of one (p1, q) share the block shape
+  if (use_even_odd(m)) return std::max(elem_eo_blocks(m), m.ncomp == 3 ? elem_blocks_bp6(m) : elem_blocks_bp5(m));
   if (m.colloc) return m.ncomp == 3 ? elem_blocks_bp6(m) : elem_blocks_bp5(m);
   return elem_blocks_bp3(m);
 }
@@ -455,9 +465,15 @@ ceedbp_status solve_mixed(ceedbp_ctx* c, const double* b, double* x, const ceedb
   int outer = 0, inner_total[3] = {0, 0, 0};
   ceedbp_status result = CEEDBP_OK;
   while (true) {
-    bool done = true;
-    for (int k = 0; k < nc; ++k)
+    bool done = true, finite = true;
+    for (int k = 0; k < nc; ++k) {
+      if (!std::isfinite(rr[k]) || !std::isfinite(bb[k])) finite = false;
       if (rr[k] > o.tol * o.tol * bb[k]) done = false;
+    }
+    if (!finite) {
+      result = CEEDBP_EBREAKDOWN;
+      break;
+    }
     if (done) break;
     if (outer >= outer_maxit) {
       result = CEEDBP_ENOCONV;
@@ -770,6 +786,14 @@ ceedbp_status ceedbp_kappa_gradient(ceedbp_ctx* c, const double* u, const double
   if (!c->colloc || c->ncomp != 1) return fail(c, CEEDBP_EUNSUPPORTED, "the adjoint gradient is built for BP5");
   if (c->p1 > 12) return fail(c, CEEDBP_EUNSUPPORTED, "the adjoint gradient is built for orders 1..11");
   CK(c, launch_kappa_grad(c->mesh, u, lam, c->d_Ghat ? c->d_Ghat : c->d_G, g, c->stream));
+  return CEEDBP_OK;
+}
+
+ceedbp_status ceedbp_tile_info(const ceedbp_ctx* c, int* eb, int* staged) {
+  if (!c) return CEEDBP_EINVAL;
+  const bool df = c->arith == CEEDBP_ARITH_DF64;
+  if (eb) *eb = df ? c->mesh.tune_eb : 0;
+  if (staged) *staged = df ? c->mesh.tune_stage : 0;
   return CEEDBP_OK;
 }
 

@@ -71,8 +71,8 @@ __global__ void batch_init_kernel(const int* __restrict__ off, const double* __r
       cs.tol2 = tol * tol * cs.bb;
       cs.alpha = cs.beta = cs.pAp = 0.0;
       cs.iters = 0;
-      cs.status = CEEDBP_OK;
-      cs.active = cs.rr > cs.tol2 ? 1 : 0;
+      cs.status = isfinite(cs.rz) && isfinite(cs.rr) ? CEEDBP_OK : CEEDBP_EBREAKDOWN;
+      cs.active = cs.status == CEEDBP_OK && cs.rr > cs.tol2 ? 1 : 0;
       if (cs.active) atomicAdd(&glob->active_count, 1);
     }
   }

@@ -59,8 +59,8 @@ __global__ void init_df_kernel(const int* __restrict__ off, const double* __rest
         cs.pAp = 0.0;
         cs.alpha = cs.beta = 0.0;
         cs.iters = 0;
-        cs.status = CEEDBP_OK;
-        cs.active = fixed ? 1 : (cs.rr > cs.tol2 ? 1 : 0);
+        cs.status = isfinite(cs.rz) && isfinite(cs.rr) && isfinite(cs.bb) ? CEEDBP_OK : CEEDBP_EBREAKDOWN;
+        cs.active = cs.status != CEEDBP_OK ? 0 : (fixed ? 1 : (cs.rr > cs.tol2 ? 1 : 0));
         any |= cs.active;
       }
       for (int c = NC; c < 3; ++c) st->c[c].active = 0;

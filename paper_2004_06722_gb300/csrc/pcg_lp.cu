@@ -102,8 +102,8 @@ __global__ void inner_init_kernel(const int* __restrict__ off, const double* __r
         cs.pAp = 0.0;
         cs.alpha = cs.beta = 0.0;
         cs.iters = 0;
-        cs.status = CEEDBP_OK;
-        cs.active = cs.rr > cs.tol2 ? 1 : 0;
+        cs.status = isfinite(cs.rz) && isfinite(cs.rr) ? CEEDBP_OK : CEEDBP_EBREAKDOWN;
+        cs.active = cs.status == CEEDBP_OK && cs.rr > cs.tol2 ? 1 : 0;
         any |= cs.active;
       }
       for (int c = NC; c < 3; ++c) st->c[c].active = 0;
