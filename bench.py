@@ -446,10 +446,105 @@ def run_batched(args):
                       "dtype": "df64 (FP32 pairs, FP64-accurate)"}), flush=True)
 
 
+def run_mixed(args):
+    """BP6 (three components), N = 7, E = 48^3, seeded RHS: plain PCG (native FP64 and FP32 pairs) against
+    FP64 defect correction with FP32 and BF16-storage inner solves, all to 1e-10 relative residual."""
+    import numpy as np
+    import torch
+
+    import paper_2004_06722_gb300 as pkg
+    from synth import uniform_pm1
+    N, E1 = 7, 48
+    coords, l2g, dirichlet = pkg.mesh_box(E1, E1, E1, N, 0.05)
+    res = {}
+    x_ref = None
+    for name, arith, mixed in [("fp64_pcg", pkg.ARITH_FP64, 0), ("df64_pcg", pkg.ARITH_DF64, 0),
+                               ("fp32_defect_correction", pkg.ARITH_DF64, pkg.MIXED_FP32),
+                               ("bf16_defect_correction", pkg.ARITH_DF64, pkg.MIXED_BF16)]:
+        op = pkg.Operator(6, N, coords, l2g, dirichlet, arith=arith)
+        if mixed:
+            op.prepare_mixed(mixed)
+        r = np.stack([uniform_pm1(c, np.arange(op.nglobal)) for c in range(3)], axis=1)
+        mask = torch.from_numpy(1.0 - dirichlet.astype(np.float64)).cuda()[:, None]
+        b = op.mass(torch.from_numpy(np.ascontiguousarray(r)).cuda()) * mask
+        op.solve(b, tol=1e-3, mixed=mixed)  # warm-up (graphs, autotuned shapes)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x, info = op.solve(b, tol=1e-10, mixed=mixed, chunk=64)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        if x_ref is None:
+            x_ref = x.clone()
+        err = (torch.linalg.norm(x - x_ref) / torch.linalg.norm(x_ref)).item()
+        res[name] = {"wall_s": wall, "device_ms": info["device_ms"], "iters": info["iters"],
+                     "outer_iters": info["outer_iters"], "rel_res": info["rel_res"],
+                     "rel_diff_vs_fp64_pcg": err}
+        op.close()
+        del b, x
+        torch.cuda.empty_cache()
+    print(json.dumps({"metric": "BP6 N=7 E=48^3 solve time to 1e-10 relative residual", "unit": "s",
+                      "higher_is_better": False, "n_per_component": E1 ** 3 * N ** 3, "results": res,
+                      "speedup_fp32_dc_vs_fp64": res["fp64_pcg"]["wall_s"] / res["fp32_defect_correction"]["wall_s"],
+                      "speedup_fp32_dc_vs_df64": res["df64_pcg"]["wall_s"] / res["fp32_defect_correction"]["wall_s"]}),
+          flush=True)
+
+
+def run_adjoint(args):
+    """-div(kappa grad u) = f, BP5 N = 7, E = 32^3, kappa = exp(g) with 16 random Fourier modes; target u*
+    from a second kappa; J = 1/2 ||u - u*||_B^2; dJ/dkappa by one adjoint solve and the fused gradient
+    kernel, checked by central differences (h = 1e-6) along 20 seeded directions."""
+    import numpy as np
+    import torch
+
+    import paper_2004_06722_gb300 as pkg
+    from synth import fourier_field, fourier_modes, uniform_pm1
+    N, E1 = 7, 32
+    coords, l2g, dirichlet = pkg.mesh_box(E1, E1, E1, N, 0.05)
+    kappa = torch.from_numpy(np.exp(fourier_field(fourier_modes(0), coords))).cuda()
+    kappa_star = torch.from_numpy(np.exp(fourier_field(fourier_modes(1), coords))).cuda()
+    op = pkg.Operator(5, N, coords, l2g, dirichlet, arith=pkg.ARITH_DF64 if args.arith == "df64" else pkg.ARITH_FP64)
+    mask = torch.from_numpy(1.0 - dirichlet.astype(np.float64)).cuda()
+    b = op.mass(torch.from_numpy(uniform_pm1(0, np.arange(op.nglobal))).cuda()) * mask
+    op.set_kappa(kappa_star)
+    u_star, _ = op.solve(b, tol=1e-13, chunk=64)
+    u_star = u_star.clone()
+    k = kappa.clone().requires_grad_(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J = pkg.kappa_misfit(k, op, b, u_star, tol=1e-10)
+    (g,) = torch.autograd.grad(J, k)
+    torch.cuda.synchronize()
+    t_grad = time.perf_counter() - t0
+
+    def Jof(kap):
+        op.set_kappa(kap)
+        u, _ = op.solve(b, tol=1e-13, chunk=64)
+        return op.misfit(u, u_star)[1]
+
+    rng = np.random.default_rng(20)
+    h, errs = 1e-6, []
+    for _ in range(20):
+        d = torch.from_numpy(rng.uniform(-1, 1, size=tuple(kappa.shape))).cuda()
+        d /= d.abs().max()
+        fd = (Jof(kappa + h * d) - Jof(kappa - h * d)) / (2 * h)
+        ad = float((g * d).sum())
+        errs.append(abs(fd - ad) / abs(ad))
+    print(json.dumps({"metric": "adjoint gradient dJ/dkappa (forward + adjoint solve to 1e-10 + gradient)",
+                      "value": t_grad, "unit": "s", "higher_is_better": False, "J": float(J),
+                      "kappa_values": int(kappa.numel()), "n": E1 ** 3 * N ** 3,
+                      "fd_rel_err_max": max(errs), "fd_rel_err_median": float(np.median(errs)),
+                      "fd_directions": 20, "h": h,
+                      "dtype": "f64" if args.arith == "fp64" else "df64 (FP32 pairs, FP64-accurate)"}), flush=True)
+
+
 def main():
     args = parse_args()
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "mixed":
+        return run_mixed(args)
+    if args.workload == "adjoint":
+        return run_adjoint(args)
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -140,6 +140,16 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsign
       : "memory");
 }
 
+// ---- per-thread asynchronous copies global -> shared (no registers in flight)
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // Bounded wait on phase `parity` of an mbarrier: returns false after `limit`
 // polls (each try_wait may itself suspend the thread for a short while).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int limit) {

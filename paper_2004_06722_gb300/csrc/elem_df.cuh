@@ -36,7 +36,9 @@ struct ElemDfShape {
   // G of an element (6 p1^3 pairs, contiguous in memory) is staged in shared
   // memory by one bulk asynchronous copy when it fits next to the tiles.
   static constexpr bool STAGE_G = STAGE && P1 <= 10;
-  static constexpr int GSTAGE = STAGE_G ? 6 * P3 : 0;  // pairs per element
+  // staged: the whole element's G; otherwise a ring of 3 slabs filled by
+  // per-thread cp.async two slabs ahead of use
+  static constexpr int GSTAGE = STAGE_G ? 6 * P3 : 3 * 6 * PP;  // pairs per element
 };
 
 template <int P1, int NC>
@@ -84,8 +86,10 @@ __device__ __forceinline__ void slot_max(unsigned* dst, float v, bool active) {
 
 constexpr int kMbarPolls = 1 << 22;
 
+// Register cap: for p1 <= 8 (one component) keep two 256-thread (or four 128-thread) blocks per SM.
 template <int P1, int NC, bool STAGE>
-__global__ void elem_df_kernel(const DeviceMesh m, const ElemDfArgs a, const int eb) {
+__global__ void __launch_bounds__(P1 <= 8 ? 256 : 1024, (P1 <= 8 && NC == 1) ? 2 : 1)
+    elem_df_kernel(const DeviceMesh m, const ElemDfArgs a, const int eb) {
   using S = ElemDfShape<P1, NC, STAGE>;
   constexpr int PP = S::PP, P3 = S::P3, ROW = S::ROW, SLAB = S::SLAB, TILE = S::TILE;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -142,6 +146,17 @@ __global__ void elem_df_kernel(const DeviceMesh m, const ElemDfArgs a, const int
   dfloat* sS = sR + NC * TILE;
   const int* l2g = m.l2g + e * P3;
   const int my = j * ROW + i;  // position of (i, j) inside a padded slab
+  if constexpr (!S::STAGE_G) {
+    if (active) {  // first two slabs of G in flight during the gather
+      const dfloat* Gg0 = a.G + size_t(e) * 6 * P3;
+#pragma unroll
+      for (int s2 = 0; s2 < 2 && s2 < P1; ++s2) {
+#pragma unroll
+        for (int q = 0; q < 6; ++q) cp_async8(sG + s2 * 6 * PP + q * PP + t, Gg0 + q * P3 + s2 * PP + t);
+        cp_async_commit();
+      }
+    }
+  }
 
   // ---- gather the column (i, j, 0..p1-1) of u^e = Q u
   dfloat xc[NC][P1];
@@ -184,29 +199,24 @@ __global__ void elem_df_kernel(const DeviceMesh m, const ElemDfArgs a, const int
       Dj[n] = sD[j * ROW + n];
     }
     const dfloat* Gg = a.G + size_t(e) * 6 * P3;
-    dfloat gnext[6];
-    if constexpr (!S::STAGE_G) {
-#pragma unroll
-      for (int q = 0; q < 6; ++q) {
-        const float2 v = __ldcs(reinterpret_cast<const float2*>(Gg + q * P3 + t));
-        gnext[q] = dfloat{v.x, v.y};
-      }
-    }
 #pragma unroll
     for (int k = 0; k < P1; ++k) {
       const int pt = k * PP + t;
       dfloat g[6];
+      if constexpr (S::STAGE_G) {
 #pragma unroll
-      for (int q = 0; q < 6; ++q) {
-        if constexpr (S::STAGE_G) {
-          g[q] = sG[q * P3 + pt];
-        } else {
-          g[q] = gnext[q];
-          if (k + 1 < P1) {  // next slab in flight while this one is used
-            const float2 v = __ldcs(reinterpret_cast<const float2*>(Gg + q * P3 + pt + PP));
-            gnext[q] = dfloat{v.x, v.y};
-          }
+        for (int q = 0; q < 6; ++q) g[q] = sG[q * P3 + pt];
+      } else {
+        if (k + 2 < P1) {
+          dfloat* ring = sG + ((k + 2) % 3) * 6 * PP;
+#pragma unroll
+          for (int q = 0; q < 6; ++q) cp_async8(ring + q * PP + t, Gg + q * P3 + pt + 2 * PP);
         }
+        cp_async_commit();
+        cp_async_wait<2>();  // this thread's copies of slab k have landed
+        const dfloat* ring = sG + (k % 3) * 6 * PP;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) g[q] = ring[q * PP + t];
       }
       const float gb = fmaxf(fmaxf(row_abs_sum3(g[0], g[1], g[2]), row_abs_sum3(g[1], g[3], g[4])),
                              row_abs_sum3(g[2], g[4], g[5]));
