@@ -48,7 +48,7 @@ def parse_args():
     ap.add_argument("--sweep-iters", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-k", type=int, default=9, help="E = 2^k elements for the oracle sample")
-    ap.add_argument("--workload", choices=["sweep", "batched", "mixed", "adjoint"], default="sweep",
+    ap.add_argument("--workload", choices=["sweep", "batched", "mixed", "adjoint", "bp-sweep"], default="sweep",
                     help="sweep: BP5 n-sweep headline; batched: 256 BP5 problems batched vs one at a time; "
                          "mixed: BP6 defect correction vs FP64 PCG; adjoint: dJ/dkappa pipeline")
     return ap.parse_args()
@@ -155,6 +155,16 @@ def n_08(ns, rates):
     return float(ns[-1])
 
 
+def max_over_ranks(ms: float, world: int, dist, device) -> float:
+    """The slowest rank's time (the whole-job time of independent replicas)."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def make_mesh(pkg, N, k):
     from synth import box_dims
     dims = box_dims(k)
@@ -199,11 +209,7 @@ def measure(pkg, args, mesh, arith, device, rank, world, dist):
     clk = clocks.stop()
     if world > 1:
         dist.barrier()
-    ms = info["device_ms"]
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(info["device_ms"], world, dist, device)
     value = world * n_dofs * K / (ms * 1e-3)
     # per-kernel durations: the same K-iteration graph with event-record nodes around each kernel
     _, pinfo = op.solve(b, x, fixed_iters=K, chunk=K, profile=True)
@@ -537,8 +543,50 @@ def run_adjoint(args):
                       "dtype": "f64" if args.arith == "fp64" else "df64 (FP32 pairs, FP64-accurate)"}), flush=True)
 
 
+def run_bp_sweep(args):
+    """BP1, BP3 and BP5 (FP64) at N in {3, 5, 7, 9, 11, 15} on E = 2^k deformed boxes with n = E N^3 stepping
+    by 2x from 1e4 to 1e8; fixed 100 PCG iterations; r_max, n_0.8 and t_0.8 = 1.25 n_0.8 / r_max per (BP, N)."""
+    import numpy as np
+    import torch
+
+    import paper_2004_06722_gb300 as pkg
+    from synth import box_dims, sweep_ks, uniform_pm1
+    iters = args.sweep_iters
+    out = {}
+    for bp in (1, 3, 5):
+        for N in (3, 5, 7, 9, 11, 15):
+            ns, rates = [], []
+            for k in sweep_ks(N):
+                dims = box_dims(k)
+                coords, l2g, dirichlet = pkg.mesh_box(*dims, N, 0.05)
+                op = pkg.Operator(bp, N, coords, l2g, dirichlet)
+                del coords, l2g
+                r = torch.from_numpy(uniform_pm1(0, np.arange(op.nglobal))).cuda()
+                mask = torch.from_numpy(1.0 - dirichlet.astype(np.float64)).cuda() if bp != 1 else 1.0
+                b = op.mass(r) * mask
+                x = op.empty()
+                op.solve(b, x, fixed_iters=iters, chunk=iters)
+                best = min(op.solve(b, x, fixed_iters=iters, chunk=iters)[1]["device_ms"] for _ in range(2))
+                n = dims[0] * dims[1] * dims[2] * N ** 3
+                ns.append(n)
+                rates.append(n * iters / (best * 1e-3))
+                op.close()
+                del b, x, r
+                torch.cuda.empty_cache()
+            rmax = max(rates)
+            n80 = n_08(ns, rates)
+            out[f"BP{bp}_N{N}"] = {"n": ns, "dofs_per_s": rates, "r_max": rmax, "n_0.8": n80,
+                                   "t_0.8_s": 1.25 * n80 / rmax}
+            print(json.dumps({f"BP{bp}_N{N}": {"r_max": rmax, "n_0.8": n80, "t_0.8_s": 1.25 * n80 / rmax}}),
+                  file=sys.stderr, flush=True)
+    print(json.dumps({"metric": "DOFs/s per CG iteration vs n (FP64), r_max, n_0.8, t_0.8 per BP and order",
+                      "unit": "DOFs/s", "iters": iters, "results": out}), flush=True)
+
+
 def main():
     args = parse_args()
+    if args.workload == "bp-sweep":
+        return run_bp_sweep(args)
     if args.workload == "batched":
         return run_batched(args)
     if args.workload == "mixed":
