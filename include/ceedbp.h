@@ -6,7 +6,9 @@
  * High-Performance PDE Solvers" (Fischer et al.), Sec. 3 and Table 1:
  *
  *   BP1  B u = r      scalar, homogeneous Neumann,   q = N+2 Gauss (GL) points
+ *   BP2  B u_i = r_i  three components, as BP1
  *   BP3  A u = r      scalar, homogeneous Dirichlet, q = N+2 GL points
+ *   BP4  A u_i = r_i  three components, as BP3
  *   BP5  A u = r      scalar, homogeneous Dirichlet, q = N+1 GLL points (collocated)
  *   BP6  A u_i = r_i  three components,  as BP5
  *
@@ -63,7 +65,7 @@ enum {
 };
 
 typedef struct {
-  int bp;           /* bake-off problem: 1, 3, 5 or 6 (Table 1) */
+  int bp;           /* bake-off problem: 1..6 (Table 1) */
   int order;        /* polynomial order N = p, 1..15; p1 = N+1 nodes per direction */
   int nquad;        /* quadrature points per direction; 0 = the BP's rule (N+2 GL or N+1 GLL) */
   int64_t nelem;    /* E, number of hexahedral elements */
@@ -113,8 +115,8 @@ ceedbp_status ceedbp_setup(const ceedbp_params* params, const double* coords,
                            const double* kappa, void* stream, ceedbp_ctx** out);
 
 /*
- * w = M A M u (BP3/5/6, M the 0/1 mask of non-Dirichlet nodes) or w = B u
- * (BP1): the assembled operator Q^T A_L Q of Eq. (21), applied matrix-free
+ * w = M A M u (BP3-BP6, M the 0/1 mask of non-Dirichlet nodes) or w = B u
+ * (BP1, BP2): the assembled operator Q^T A_L Q of Eq. (21), applied matrix-free
  * with the element operator of Eq. (22) (or Eq. (34)) and a deterministic
  * gather-scatter sum over sorted element slots (no floating-point atomics).
  * u_dev, w_dev: device FP64 [nglobal][ncomp]; they must not overlap.

@@ -5,6 +5,8 @@ Table 1 and Sec. 3:
 * BP1: B u = r, scalar, homogeneous Neumann, q = p+2 GL quadrature.
 * BP3: A u = r, scalar, homogeneous Dirichlet, q = p+2 GL quadrature.
 * BP5: A u = r, scalar, homogeneous Dirichlet, q = p+1 GLL quadrature (collocated).
+* BP2: B u_i = r_i, three components, as BP1 (independent copies sharing the mesh).
+* BP4: A u_i = r_i, three components, as BP3.
 * BP6: A u_i = r_i, three components, as BP5; the components are independent
   copies of BP5 sharing the mesh and geometry.
 
@@ -31,17 +33,18 @@ from .quadrature import bp_rule
 class BakeoffProblem:
     def __init__(self, bp: int, Ex: int, Ey: int, Ez: int, N: int, amp: float = 0.05,
                  kappa: np.ndarray | None = None, rule=None):
-        if bp not in (1, 3, 5, 6):
-            raise ValueError("oracle covers BP1, BP3, BP5 and BP6")
+        if bp not in (1, 2, 3, 4, 5, 6):
+            raise ValueError("bake-off problems are BP1..BP6")
         self.bp, self.N = bp, N
         self.dims = (Ex, Ey, Ez)
-        self.ncomp = 3 if bp == 6 else 1
+        self.ncomp = 3 if bp in (2, 4, 6) else 1
         self.rule = bp_rule(bp, N) if rule is None else rule
         self.q = len(self.rule[0])
         self.coords, self.l2g = box_mesh(Ex, Ey, Ez, N, amp)
         self.n_global = global_count(Ex, Ey, Ez, N)
         E = Ex * Ey * Ez
-        want = ("B",) if bp == 1 else ("A", "B")
+        mass_only = bp in (1, 2)
+        want = ("B",) if mass_only else ("A", "B")
         Ae, Be = [], []
         for e in range(E):
             k_e = None if kappa is None else kappa[e]
@@ -50,8 +53,8 @@ class BakeoffProblem:
             if "A" in m:
                 Ae.append(m["A"])
         self.B = assemble(self.l2g, Be, self.n_global)
-        self.A = self.B if bp == 1 else assemble(self.l2g, Ae, self.n_global)
-        if bp == 1:
+        self.A = self.B if mass_only else assemble(self.l2g, Ae, self.n_global)
+        if mass_only:
             self.free = np.ones(self.n_global, dtype=bool)
         else:
             self.free = ~boundary_nodes(Ex, Ey, Ez, N)
@@ -72,7 +75,7 @@ class BakeoffProblem:
 
     # -- operators ----------------------------------------------------------------
     def apply(self, u: np.ndarray) -> np.ndarray:
-        """w = M A M u (BP3/5/6) or w = B u (BP1), all components."""
+        """w = M A M u (BP3-BP6) or w = B u (BP1, BP2), all components."""
         return masked_apply(self.A, self.free, u)
 
     def mass(self, u: np.ndarray) -> np.ndarray:

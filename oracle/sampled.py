@@ -29,7 +29,7 @@ def sampled_rows(bp: int, Ex: int, Ey: int, Ez: int, N: int, amp: float, u_of, n
     rule = bp_rule(bp, N)
     elems = elements_touching(Ex, Ey, Ez, N, nodes)
     coords, l2g = box_mesh(Ex, Ey, Ez, N, amp, elements=elems)
-    dirichlet = bp != 1 and operator == "A"
+    dirichlet = bp not in (1, 2) and operator == "A"
     out = None
     where = {int(g): i for i, g in enumerate(nodes)}
     for el in range(len(elems)):
@@ -37,7 +37,7 @@ def sampled_rows(bp: int, Ex: int, Ey: int, Ez: int, N: int, amp: float, u_of, n
         hit = [a for a, g in enumerate(idx) if int(g) in where]
         if not hit:
             continue
-        which = "B" if (bp == 1 or operator == "B") else "A"
+        which = "B" if (bp in (1, 2) or operator == "B") else "A"
         kap = None if kappa_of is None else kappa_of(int(elems[el]))
         M = element_matrices(coords[el], N, rule, kappa=kap, want=(which,))[which]
         ue = np.asarray(u_of(idx), dtype=np.float64)

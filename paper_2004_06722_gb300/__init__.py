@@ -134,7 +134,7 @@ class Operator:
         # a dedicated stream: CUDA graphs cannot be captured on the legacy default stream
         self.stream = torch.cuda.Stream(self.device) if stream is None else stream
         self.bp, self.order = bp, order
-        self.ncomp = 3 if bp == 6 else 1
+        self.ncomp = 3 if bp in (2, 4, 6) else 1
         coords = np.ascontiguousarray(coords, dtype=np.float64)
         l2g = np.ascontiguousarray(l2g, dtype=np.int64)
         self.nelem = coords.shape[0]

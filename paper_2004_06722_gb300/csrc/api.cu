@@ -17,6 +17,9 @@ cudaError_t launch_elem_bp3(const DeviceMesh& m, const ElemArgs& a, cudaStream_t
 cudaError_t launch_elem_bp5(const DeviceMesh& m, const ElemArgs& a, cudaStream_t s);
 cudaError_t launch_elem_bp6(const DeviceMesh& m, const ElemArgs& a, cudaStream_t s);
 int elem_blocks_bp1(const DeviceMesh& m);
+cudaError_t launch_elem_bp2(const DeviceMesh& m, const ElemArgs& a, cudaStream_t s);
+cudaError_t launch_elem_bp4(const DeviceMesh& m, const ElemArgs& a, cudaStream_t s);
+int elem_blocks_bp4(const DeviceMesh& m);
 int elem_blocks_bp3(const DeviceMesh& m);
 int elem_blocks_bp5(const DeviceMesh& m);
 int elem_blocks_bp6(const DeviceMesh& m);
@@ -32,8 +35,8 @@ static bool use_even_odd(const DeviceMesh& m) { return m.colloc && (m.p1 % 2 == 
 cudaError_t launch_elem(const DeviceMesh& m, int kind, const ElemArgs& a, cudaStream_t s) {
   if (kind == kStiff && use_even_odd(m)) return launch_elem_eo(m, a, s);
   if (m.colloc && kind == kStiff) return m.ncomp == 3 ? launch_elem_bp6(m, a, s) : launch_elem_bp5(m, a, s);
-  if (!m.colloc && kind == kStiff && m.ncomp == 1) return launch_elem_bp3(m, a, s);
-  if (!m.colloc && kind == kMass && m.ncomp == 1) return launch_elem_bp1(m, a, s);
+  if (!m.colloc && kind == kStiff) return m.ncomp == 3 ? launch_elem_bp4(m, a, s) : launch_elem_bp3(m, a, s);
+  if (!m.colloc && kind == kMass) return m.ncomp == 3 ? launch_elem_bp2(m, a, s) : launch_elem_bp1(m, a, s);
   return cudaErrorInvalidValue;
 }
 
@@ -41,7 +44,7 @@ int elem_blocks(const DeviceMesh& m) {
   // stiffness and mass instantiations of one (p1, q) share the block shape
   if (use_even_odd(m)) return std::max(elem_eo_blocks(m), m.ncomp == 3 ? elem_blocks_bp6(m) : elem_blocks_bp5(m));
   if (m.colloc) return m.ncomp == 3 ? elem_blocks_bp6(m) : elem_blocks_bp5(m);
-  return elem_blocks_bp3(m);
+  return m.ncomp == 3 ? elem_blocks_bp4(m) : elem_blocks_bp3(m);
 }
 }  // namespace ceedbp
 
@@ -96,7 +99,7 @@ void release(ceedbp_ctx* c) {
 ceedbp_status setup_impl(ceedbp_ctx* c, const double* coords, const int64_t* l2g, const uint8_t* dirichlet,
                          const double* kappa) {
   const ceedbp_params& P = c->prm;
-  if (P.bp != 1 && P.bp != 3 && P.bp != 5 && P.bp != 6) return fail(c, CEEDBP_EUNSUPPORTED, "bp must be 1, 3, 5 or 6");
+  if (P.bp < 1 || P.bp > 6) return fail(c, CEEDBP_EUNSUPPORTED, "bp must be 1..6");
   if (P.order < 1 || P.order > kMaxOrder) return fail(c, CEEDBP_EINVAL, "order must be in 1..15");
   if (P.nelem < 1 || P.nglobal < 1) return fail(c, CEEDBP_EINVAL, "nelem and nglobal must be positive");
   if (!coords || !l2g) return fail(c, CEEDBP_EINVAL, "coords and l2g are required");
@@ -110,13 +113,13 @@ ceedbp_status setup_impl(ceedbp_ctx* c, const double* coords, const int64_t* l2g
   c->p1 = p1;
   c->q = qdef;
   c->colloc = gll_quad;
-  c->ncomp = P.bp == 6 ? 3 : 1;
-  c->op_kind = P.bp == 1 ? kMass : kStiff;
+  c->ncomp = (P.bp == 2 || P.bp == 4 || P.bp == 6) ? 3 : 1;
+  c->op_kind = (P.bp == 1 || P.bp == 2) ? kMass : kStiff;
   const int64_t P3 = int64_t(p1) * p1 * p1, Q3 = int64_t(qdef) * qdef * qdef;
   const int64_t nloc = P.nelem * P3;
   if (nloc >= (int64_t(1) << 31) || P.nglobal >= (int64_t(1) << 31) - 1)
     return fail(c, CEEDBP_EINVAL, "problem too large for 32-bit local indices (E p1^3 and nglobal must stay below 2^31)");
-  const bool masked = P.bp != 1 && dirichlet != nullptr;
+  const bool masked = P.bp != 1 && P.bp != 2 && dirichlet != nullptr;
   if (P.arith != CEEDBP_ARITH_FP64 && P.arith != CEEDBP_ARITH_DF64) return fail(c, CEEDBP_EINVAL, "unknown arith");
   if (P.arith == CEEDBP_ARITH_DF64 && !gll_quad)
     return fail(c, CEEDBP_EUNSUPPORTED, "the FP32-pair arithmetic is built for BP5 and BP6 only");
@@ -612,7 +615,7 @@ ceedbp_status ceedbp_apply(ceedbp_ctx* c, const double* u, double* w) {
   a.u = u;
   a.wl = c->d_wl;
   a.G = c->op_kind == kStiff ? c->d_G : c->d_Mq;
-  a.mask_in = c->prm.bp != 1;
+  a.mask_in = c->prm.bp != 1 && c->prm.bp != 2;
   a.skip_dirichlet_out = 1;
   CK(c, launch_elem(c->mesh, c->op_kind, a, c->stream));
   CK(c, launch_gs(c->mesh, c->d_wl, w, 1, c->stream));

@@ -44,6 +44,8 @@ CASES = [
     (3, 1, (3, 2, 2)), (3, 2, (2, 3, 2)), (3, 3, (3, 2, 2)), (3, 5, (2, 2, 1)), (3, 7, (2, 1, 1)), (3, 11, (1, 1, 1)),
     (1, 1, (2, 2, 3)), (1, 3, (3, 2, 2)), (1, 5, (2, 2, 1)), (1, 7, (2, 1, 1)), (1, 15, (1, 1, 1)),
     (6, 2, (2, 2, 2)), (6, 3, (3, 2, 2)), (6, 7, (2, 1, 1)),
+    (2, 1, (2, 2, 2)), (2, 3, (3, 2, 2)), (2, 7, (2, 1, 1)),
+    (4, 2, (2, 2, 2)), (4, 3, (3, 2, 2)), (4, 7, (2, 1, 1)),
 ]
 
 
@@ -67,7 +69,7 @@ def test_apply_parity(problems, bp, N, dims):
     w = op.apply(torch.from_numpy(u).cuda()).cpu().numpy()
     w_ref = ref.apply(u)
     assert _rel(w, w_ref) < APPLY_TOL
-    if bp != 1:
+    if bp not in (1, 2):
         assert np.all(w.reshape(op.nglobal, -1)[boundary_nodes(*dims, N)] == 0)
 
 
@@ -83,7 +85,8 @@ def test_mass_and_jacobi_parity(problems, bp, N, dims):
 
 
 @pytest.mark.parametrize("bp,N,dims", [(5, 3, (3, 2, 2)), (5, 7, (2, 2, 2)), (3, 3, (2, 2, 2)), (1, 4, (2, 2, 2)),
-                                        (6, 3, (2, 2, 2)), (5, 2, (4, 3, 3))])
+                                        (6, 3, (2, 2, 2)), (5, 2, (4, 3, 3)), (2, 3, (2, 2, 2)),
+                                        (4, 3, (2, 2, 2))])
 def test_solve_parity(problems, bp, N, dims):
     op, ref = problems(bp, N, dims)
     r = _vec(op.nglobal, op.ncomp, 0)
