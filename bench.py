@@ -141,6 +141,18 @@ def bp5_units(N: int):
     return elem_bytes, iter_bytes, elem_flops
 
 
+def bp5_units_recompute(N: int):
+    """As bp5_units with the factors recomputed in the element kernel: three coordinate words per
+    local node replace the six factor words; flops add the Jacobian (9 contractions, 18 p1 per node)
+    and adj(J), |J| and the six factors (71 per node)."""
+    p1 = N + 1
+    ratio = (p1 / N) ** 3
+    elem_bytes = 8 * 2 + (3 * 8 + 4) * ratio
+    iter_bytes = 8 * 13 + (3 * 8 + 4) * ratio
+    elem_flops = (30 * p1 ** 4 + 86 * p1 ** 3) / N ** 3
+    return elem_bytes, iter_bytes, elem_flops
+
+
 def n_08(ns, rates):
     """Smallest n with rate >= 0.8 r_max, log-linearly interpolated between samples."""
     rmax = max(rates)
@@ -172,13 +184,13 @@ def make_mesh(pkg, N, k):
     return dims, coords, l2g, dirichlet
 
 
-def make_problem(pkg, N, mesh, seed, device, arith=0):
+def make_problem(pkg, N, mesh, seed, device, arith=0, geom=0):
     import numpy as np
     import torch
 
     from synth import uniform_pm1
     dims, coords, l2g, dirichlet = mesh
-    op = pkg.Operator(5, N, coords, l2g, dirichlet, device=device, arith=arith)
+    op = pkg.Operator(5, N, coords, l2g, dirichlet, device=device, arith=arith, geom=geom)
     r = torch.from_numpy(uniform_pm1(seed, np.arange(op.nglobal))).to(device)
     mask = torch.from_numpy(1.0 - dirichlet.astype(np.float64)).to(device)
     b = op.mass(r) * mask
@@ -186,11 +198,11 @@ def make_problem(pkg, N, mesh, seed, device, arith=0):
     return op, b, E * N ** 3
 
 
-def measure(pkg, args, mesh, arith, device, rank, world, dist):
+def measure(pkg, args, mesh, arith, device, rank, world, dist, geom=0):
     """One arithmetic variant at the headline size: timed graph, per-kernel profile, end-to-end."""
     import torch
     N, K, W = args.order, args.steps, max(3, args.warmup)
-    op, b, n_dofs = make_problem(pkg, N, mesh, seed=rank, device=device, arith=arith)
+    op, b, n_dofs = make_problem(pkg, N, mesh, seed=rank, device=device, arith=arith, geom=geom)
     dims = mesh[0]
     x = op.empty()
     op.solve(b, x, fixed_iters=K, chunk=K)  # graph capture for the timed chunk length
@@ -230,16 +242,18 @@ def measure(pkg, args, mesh, arith, device, rank, world, dist):
     e2e_ms = ev0.elapsed_time(ev1)
 
     peaks, peak_src = load_peaks()
-    elem_bytes_dof, iter_bytes_dof, elem_flops_dof = bp5_units(N)
+    rc = geom == pkg.GEOM_RECOMPUTE
+    elem_bytes_dof, iter_bytes_dof, elem_flops_dof = bp5_units_recompute(N) if rc else bp5_units(N)
     fp64_tf, fp64_src = fp64_peak_tflops(peaks)
     elem_flops = elem_flops_dof * n_dofs
     elem_bytes = elem_bytes_dof * n_dofs
-    name = "fp64" if arith == pkg.ARITH_FP64 else "df64"
+    name = ("fp64rc" if rc else "fp64") if arith == pkg.ARITH_FP64 else "df64"
     traffic = ncu_traffic(f"bk5_{name}_n{N}.md")
     if arith == pkg.ARITH_FP64:
         ach = elem_flops / (elem_ms * 1e-3) / 1e12
+        kname = "elem_rc_kernel (BK5, FP64, factors recomputed)" if rc else "elem_eo_kernel (BK5, FP64, even-odd)"
         roof = {"bound": "alu", "achieved": ach, "peak": fp64_tf, "unit": "TFLOP/s", "frac": ach / fp64_tf,
-                "traffic": traffic, "kernel": "elem_kernel (BK5, FP64)", "peak_source": fp64_src,
+                "traffic": traffic, "kernel": kname, "peak_source": fp64_src,
                 "hbm_frac": (elem_bytes / (elem_ms * 1e-3) / 1e9) / peaks["hbm_gbs"]}
     else:
         ach = elem_bytes / (elem_ms * 1e-3) / 1e9
@@ -294,6 +308,8 @@ def run_ours(args):
         other = pkg.ARITH_FP64 if head_arith == pkg.ARITH_DF64 else pkg.ARITH_DF64
         variants["df64" if other == pkg.ARITH_DF64 else "fp64"] = measure(pkg, args, mesh, other, device, rank,
                                                                            world, dist)
+        variants["fp64_recompute"] = measure(pkg, args, mesh, pkg.ARITH_FP64, device, rank, world, dist,
+                                             geom=pkg.GEOM_RECOMPUTE)
     dims, n_dofs = head["elements"], head["n"]
     line = {
         "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
@@ -534,22 +550,34 @@ def run_adjoint(args):
     (g13,) = torch.autograd.grad(pkg.kappa_misfit(k13, op, b, u_star, tol=1e-13), k13)
 
     rng = np.random.default_rng(20)
-    h, errs, errs13, cancel = 1e-6, [], [], []
+    h, errs, errs13, cancel, scaled = 1e-6, [], [], [], []
     for _ in range(20):
         d = torch.from_numpy(rng.uniform(-1, 1, size=tuple(kappa.shape))).cuda()
         d /= d.abs().max()
         fd = (Jof(kappa + h * d) - Jof(kappa - h * d)) / (2 * h)
         ad, ad13 = float((g * d).sum()), float((g13 * d).sum())
+        mag = float((g13 * d).abs().sum())
         errs.append(abs(fd - ad) / abs(ad))
         errs13.append(abs(fd - ad13) / abs(ad13))
-        cancel.append(float((g13 * d).abs().sum()) / abs(ad13))
+        cancel.append(mag / abs(ad13))
+        scaled.append(abs(fd - ad) / mag)
+    # smooth directions: log-kappa perturbations of the same Fourier form as g (seeds 100..104)
+    smooth = []
+    for sd in range(100, 105):
+        d = torch.from_numpy(fourier_field(fourier_modes(sd), coords)).cuda()
+        d /= d.abs().max()
+        fd = (Jof(kappa + h * d * kappa) - Jof(kappa - h * d * kappa)) / (2 * h)
+        ad = float((g * d * kappa).sum())
+        smooth.append(abs(fd - ad) / abs(ad))
     print(json.dumps({"metric": "adjoint gradient dJ/dkappa (forward + adjoint solve to 1e-10 + gradient)",
                       "value": t_grad, "unit": "s", "higher_is_better": False, "J": float(J.detach()),
                       "kappa_values": int(kappa.numel()), "n": E1 ** 3 * N ** 3,
                       "fd_rel_err_max": max(errs), "fd_rel_err_median": float(np.median(errs)),
                       "fd_rel_err_max_tol13": max(errs13), "fd_rel_err_median_tol13": float(np.median(errs13)),
-                      "cancellation_max": max(cancel), "fd_directions": 20, "h": h,
-                      "dtype": "f64" if args.arith == "fp64" else "df64 (FP32 pairs, FP64-accurate)"}), flush=True)
+                      "cancellation_max": max(cancel), "fd_err_over_abs_sum_max": max(scaled),
+                      "fd_rel_err_smooth_max": max(smooth), "fd_directions": 20, "smooth_directions": 5,
+                      "h": h, "dtype": "f64" if args.arith == "fp64" else "df64 (FP32 pairs, FP64-accurate)"}),
+          flush=True)
 
 
 def run_bp_sweep(args):

@@ -71,7 +71,25 @@ typedef struct {
   int64_t nelem;    /* E, number of hexahedral elements */
   int64_t nglobal;  /* number of unique nodes */
   int arith;        /* CEEDBP_ARITH_FP64 or CEEDBP_ARITH_DF64 (apply and solve) */
+  int geom;         /* CEEDBP_GEOM_STORED (0) or CEEDBP_GEOM_RECOMPUTE (see below) */
 } ceedbp_params;
+
+/*
+ * Geometric factors (Eq. (23)).  STORED keeps the six factors per quadrature
+ * point in device memory (48 bytes per point) and streams them every apply.
+ * RECOMPUTE keeps the nodal coordinates instead (24 bytes per node, layout
+ * [E][3][p1^3]) and forms J, adj(J), |J| and the factors inside the element
+ * kernel each apply (about 9 p1 + 40 more FMAs per node).  RECOMPUTE is built
+ * for BP5 and BP6 (collocated GLL quadrature, where the Jacobian at a node is
+ * the derivative of the map of Eq. (18) with the operator's own D), with FP64
+ * arithmetic, without kappa, and for BP6 up to order 12; setup returns
+ * CEEDBP_EUNSUPPORTED otherwise.  The Jacobi diagonal is computed at setup
+ * from temporary stored factors.  Defect correction, set_kappa and the
+ * adjoint gradient need the stored factors and return CEEDBP_EUNSUPPORTED on
+ * a RECOMPUTE context.
+ */
+#define CEEDBP_GEOM_STORED 0
+#define CEEDBP_GEOM_RECOMPUTE 1
 
 /*
  * Deformed-box mesh helper (Sec. 3: E elements in a tensor-product array;

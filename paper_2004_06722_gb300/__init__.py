@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_PKG, "libceedbp.so")
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, EBREAKDOWN, EUNSUPPORTED = range(7)
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "EBREAKDOWN", 6: "EUNSUPPORTED"}
 ARITH_FP64, ARITH_DF64 = 0, 1
+GEOM_STORED, GEOM_RECOMPUTE = 0, 1
 MIXED_NONE, MIXED_FP32, MIXED_BF16 = 0, 1, 2
 
 
@@ -30,7 +31,8 @@ class CeedbpError(RuntimeError):
 
 class Params(ctypes.Structure):
     _fields_ = [("bp", ctypes.c_int), ("order", ctypes.c_int), ("nquad", ctypes.c_int),
-                ("nelem", ctypes.c_int64), ("nglobal", ctypes.c_int64), ("arith", ctypes.c_int)]
+                ("nelem", ctypes.c_int64), ("nglobal", ctypes.c_int64), ("arith", ctypes.c_int),
+                ("geom", ctypes.c_int)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -125,7 +127,8 @@ class Operator:
     """One bake-off problem on the GPU: ceedbp_setup / apply / mass / solve / destroy."""
 
     def __init__(self, bp: int, order: int, coords: np.ndarray, l2g: np.ndarray, dirichlet: np.ndarray | None,
-                 kappa: np.ndarray | None = None, stream=None, device=None, arith: int = 0):
+                 kappa: np.ndarray | None = None, stream=None, device=None, arith: int = 0,
+                 geom: int = 0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("ceedbp needs a CUDA device; there is no CPU path")
@@ -147,8 +150,8 @@ class Operator:
             raise ValueError(f"kappa must hold E * {q ** 3} values")
         dirichlet = None if dirichlet is None else np.ascontiguousarray(dirichlet, dtype=np.uint8)
         kappa = None if kappa is None else np.ascontiguousarray(kappa, dtype=np.float64)
-        self.arith = arith
-        prm = Params(bp, order, 0, self.nelem, self.nglobal, arith)
+        self.arith, self.geom = arith, geom
+        prm = Params(bp, order, 0, self.nelem, self.nglobal, arith, geom)
         ctx = ctypes.c_void_p()
         cur = torch.cuda.current_stream(self.device)
         self.stream.wait_stream(cur)

@@ -33,6 +33,7 @@ bool elem_eo_available(const DeviceMesh& m);
 static bool use_even_odd(const DeviceMesh& m) { return m.colloc && (m.p1 % 2 == 0) && elem_eo_available(m); }
 
 cudaError_t launch_elem(const DeviceMesh& m, int kind, const ElemArgs& a, cudaStream_t s) {
+  if (kind == kStiff && m.X != nullptr) return launch_elem_rc(m, a, s);
   if (kind == kStiff && use_even_odd(m)) return launch_elem_eo(m, a, s);
   if (m.colloc && kind == kStiff) return m.ncomp == 3 ? launch_elem_bp6(m, a, s) : launch_elem_bp5(m, a, s);
   if (!m.colloc && kind == kStiff) return m.ncomp == 3 ? launch_elem_bp4(m, a, s) : launch_elem_bp3(m, a, s);
@@ -42,6 +43,7 @@ cudaError_t launch_elem(const DeviceMesh& m, int kind, const ElemArgs& a, cudaSt
 
 int elem_blocks(const DeviceMesh& m) {
   // stiffness and mass instantiations of one (p1, q) share the block shape
+  if (m.X != nullptr) return elem_rc_blocks(m);
   if (use_even_odd(m)) return std::max(elem_eo_blocks(m), m.ncomp == 3 ? elem_blocks_bp6(m) : elem_blocks_bp5(m));
   if (m.colloc) return m.ncomp == 3 ? elem_blocks_bp6(m) : elem_blocks_bp5(m);
   return m.ncomp == 3 ? elem_blocks_bp4(m) : elem_blocks_bp3(m);
@@ -84,7 +86,7 @@ void release(ceedbp_ctx* c) {
   void* ptrs[] = {c->d_l2g, c->d_off, c->d_slots, c->d_basis, c->d_G, c->d_Mq, c->d_dinv, c->d_mdiag,
                   c->d_wl, c->d_r, c->d_p, c->d_ax, c->d_part_apply, c->d_part_vec, c->d_state,
                   c->d_Gdf, c->d_Ddf, c->d_dinvdf, c->d_G32, c->d_Gbf, c->d_dinv32, c->d_xin,
-                  c->d_rin, c->d_pin, c->d_outer, c->d_Ghat, c->d_scal};
+                  c->d_rin, c->d_pin, c->d_outer, c->d_Ghat, c->d_scal, c->d_X};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_outer) cudaFreeHost(c->h_outer);
@@ -124,6 +126,14 @@ ceedbp_status setup_impl(ceedbp_ctx* c, const double* coords, const int64_t* l2g
   if (P.arith == CEEDBP_ARITH_DF64 && !gll_quad)
     return fail(c, CEEDBP_EUNSUPPORTED, "the FP32-pair arithmetic is built for BP5 and BP6 only");
   c->arith = P.arith;
+  if (P.geom != CEEDBP_GEOM_STORED && P.geom != CEEDBP_GEOM_RECOMPUTE) return fail(c, CEEDBP_EINVAL, "unknown geom");
+  const bool recompute = P.geom == CEEDBP_GEOM_RECOMPUTE;
+  if (recompute) {
+    if (!gll_quad || P.arith != CEEDBP_ARITH_FP64 || kappa != nullptr)
+      return fail(c, CEEDBP_EUNSUPPORTED, "recomputed factors are built for BP5/BP6, FP64, without kappa");
+    if (!elem_rc_supported(p1, c->ncomp))
+      return fail(c, CEEDBP_EUNSUPPORTED, "recomputed factors: the element tile does not fit at this order");
+  }
 
   // ---- host: encoded l2g, CSR of local slots per global node (counting sort, slots ascending)
   std::vector<int> hl2g(nloc), hoff(P.nglobal + 1, 0), hslots(nloc);
@@ -215,6 +225,10 @@ ceedbp_status setup_impl(ceedbp_ctx* c, const double* coords, const int64_t* l2g
     } else {
       e = launch_geom(m, d_coords, nullptr, c->d_G, c->d_Mq, d_scratch, s);
     }
+    if (e == cudaSuccess && recompute) {
+      e = dalloc(&c->d_X, size_t(nloc) * 3);
+      if (e == cudaSuccess) e = launch_coords_soa(d_coords, c->d_X, P.nelem, int(P3), s);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(d_coords);
     cudaFree(d_scratch);
@@ -237,6 +251,19 @@ ceedbp_status setup_impl(ceedbp_ctx* c, const double* coords, const int64_t* l2g
     m1.ncomp = 1;
     CK(c, launch_local_diag(m1, kMass, nullptr, c->d_Mq, c->d_wl, s));
     CK(c, launch_gs(m1, c->d_wl, c->d_mdiag, 0, s));
+  }
+  if (recompute) {
+    // from here on the element kernel forms G from the coordinates
+    CK(c, cudaStreamSynchronize(s));
+    cudaFree(c->d_G);
+    c->d_G = nullptr;
+    m.X = c->d_X;
+    int nb = elem_blocks(m);
+    if (nb > nb_apply) {
+      cudaFree(c->d_part_apply);
+      c->d_part_apply = nullptr;
+      CK(c, dalloc(&c->d_part_apply, size_t(nb) * nc));
+    }
   }
   // One launch of every element kernel this context uses, so that their
   // one-time attribute setup happens here and never inside a graph capture.
@@ -550,6 +577,7 @@ ceedbp_status ceedbp_prepare_mixed(ceedbp_ctx* c, int precision) {
   if (precision != CEEDBP_MIXED_FP32 && precision != CEEDBP_MIXED_BF16)
     return fail(c, CEEDBP_EINVAL, "precision must be CEEDBP_MIXED_FP32 or CEEDBP_MIXED_BF16");
   if (!c->colloc) return fail(c, CEEDBP_EUNSUPPORTED, "defect correction is built for BP5 and BP6");
+  if (c->d_X) return fail(c, CEEDBP_EUNSUPPORTED, "this call needs stored geometric factors (geom = STORED)");
   const int64_t n = c->prm.nglobal, nc = c->ncomp;
   const int64_t ng = c->prm.nelem * 6 * int64_t(c->q) * c->q * c->q;
   cudaStream_t s = c->stream;
@@ -748,6 +776,7 @@ ceedbp_status ceedbp_solve(ceedbp_ctx* c, const double* b, double* x, const ceed
 ceedbp_status ceedbp_set_kappa(ceedbp_ctx* c, const double* kappa) {
   if (!c || !kappa) return fail(c, CEEDBP_EINVAL, "null argument");
   if (c->op_kind != kStiff) return fail(c, CEEDBP_EUNSUPPORTED, "kappa applies to stiffness problems");
+  if (c->d_X) return fail(c, CEEDBP_EUNSUPPORTED, "this call needs stored geometric factors (geom = STORED)");
   cudaStream_t s = c->stream;
   const int64_t q3 = int64_t(c->q) * c->q * c->q;
   const size_t ng = size_t(c->prm.nelem) * 6 * q3;
@@ -788,6 +817,7 @@ ceedbp_status ceedbp_kappa_gradient(ceedbp_ctx* c, const double* u, const double
   if (!c || !u || !lam || !g) return fail(c, CEEDBP_EINVAL, "null argument");
   if (!c->colloc || c->ncomp != 1) return fail(c, CEEDBP_EUNSUPPORTED, "the adjoint gradient is built for BP5");
   if (c->p1 > 12) return fail(c, CEEDBP_EUNSUPPORTED, "the adjoint gradient is built for orders 1..11");
+  if (c->d_X) return fail(c, CEEDBP_EUNSUPPORTED, "this call needs stored geometric factors (geom = STORED)");
   CK(c, launch_kappa_grad(c->mesh, u, lam, c->d_Ghat ? c->d_Ghat : c->d_G, g, c->stream));
   return CEEDBP_OK;
 }

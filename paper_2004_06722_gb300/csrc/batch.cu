@@ -277,6 +277,8 @@ ceedbp_status ceedbp_batch_setup(int nprob, const ceedbp_params* params, const d
   std::map<int, std::vector<int>> by_order;
   for (int p = 0; p < nprob; ++p) {
     if (params[p].bp != 5) return fail_out(bfail(nullptr, CEEDBP_EUNSUPPORTED, "batched solves are built for BP5"));
+    if (params[p].geom != CEEDBP_GEOM_STORED)
+      return fail_out(bfail(nullptr, CEEDBP_EUNSUPPORTED, "batched solves use stored geometric factors"));
     if (params[p].order < 1 || params[p].order > kMaxOrder)
       return fail_out(bfail(nullptr, CEEDBP_EINVAL, "order must be in 1..15"));
     by_order[params[p].order].push_back(p);

@@ -26,6 +26,7 @@ struct ceedbp_ctx {
   int* d_slots = nullptr;
   double* d_basis = nullptr;
   double* d_G = nullptr;
+  double* d_X = nullptr;  // [E][3][p1^3] coordinates when the factors are recomputed
   double* d_Mq = nullptr;
   double* d_dinv = nullptr;
   double* d_mdiag = nullptr;

@@ -79,6 +79,7 @@ struct DeviceMesh {
   const double* basis;  // device 1D tables (layout above)
   int tune_eb;          // elements per block of the FP32-pair kernel (0 = default; set by the autotuner)
   int tune_stage;       // 1: stage G in shared memory with a bulk copy (autotuner), 0: register prefetch
+  const double* X;      // [E][3][p1^3] nodal coordinates when the factors are recomputed, else nullptr
 };
 
 // ---- kernel launchers (one translation unit per family) ----------------------
@@ -106,6 +107,12 @@ struct ElemArgs {
 };
 int elem_blocks(const DeviceMesh& m);
 cudaError_t launch_elem(const DeviceMesh& m, int kind, const ElemArgs& a, cudaStream_t s);
+// Stiffness element kernel recomputing G from m.X (collocated, FP64).
+cudaError_t launch_elem_rc(const DeviceMesh& m, const ElemArgs& a, cudaStream_t s);
+int elem_rc_blocks(const DeviceMesh& m);
+bool elem_rc_supported(int p1, int ncomp);
+// coords [E][p1^3][3] -> X [E][3][p1^3]
+cudaError_t launch_coords_soa(const double* coords, double* X, int64_t nelem, int p3, cudaStream_t s);
 
 // Gather-scatter sum w[g] = sum_slots wl (masked on Dirichlet nodes if mask_out).
 cudaError_t launch_gs(const DeviceMesh& m, const double* wl, double* w, int mask_out, cudaStream_t s);

@@ -176,8 +176,9 @@ def test_invalid_setup_is_rejected():
     with pytest.raises(pkg.CeedbpError) as ei:
         pkg.Operator(5, 2, coords, bad, dirichlet)
     assert ei.value.status == pkg.EINVAL
-    with pytest.raises(pkg.CeedbpError):
-        pkg.Operator(4, 2, coords, l2g, dirichlet)
+    with pytest.raises(pkg.CeedbpError) as ei:
+        pkg.Operator(7, 2, coords, l2g, dirichlet)
+    assert ei.value.status == pkg.EUNSUPPORTED
 
 
 @pytest.mark.parametrize("bp,N,k", [(5, 7, 18), (3, 15, 14), (1, 3, 21)])
