@@ -46,6 +46,10 @@ def parse_args():
     ap.add_argument("--k", type=int, default=18, help="E = 2^k elements (N=7: k=18 is n = 8.99e7)")
     ap.add_argument("--no-sweep", action="store_true", help="skip the n sweep (r_max, n_0.8, t_0.8)")
     ap.add_argument("--sweep-iters", type=int, default=100)
+    ap.add_argument("--df-tile", default=None,
+                    help="pin the pair kernel's shape 'eb,schedule,seq' instead of the autotuner's choice")
+    ap.add_argument("--geom", choices=["stored", "recompute"], default="stored",
+                    help="geometric factors of the headline arm: stored, or recomputed in the element kernel")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-k", type=int, default=9, help="E = 2^k elements for the oracle sample")
     ap.add_argument("--workload", choices=["sweep", "batched", "mixed", "adjoint", "bp-sweep"], default="sweep",
@@ -203,6 +207,8 @@ def measure(pkg, args, mesh, arith, device, rank, world, dist, geom=0):
     import torch
     N, K, W = args.order, args.steps, max(3, args.warmup)
     op, b, n_dofs = make_problem(pkg, N, mesh, seed=rank, device=device, arith=arith, geom=geom)
+    if arith == pkg.ARITH_DF64 and args.df_tile:
+        op.set_tile(*[int(v) for v in args.df_tile.split(",")])
     dims = mesh[0]
     x = op.empty()
     op.solve(b, x, fixed_iters=K, chunk=K)  # graph capture for the timed chunk length
@@ -280,8 +286,10 @@ def measure(pkg, args, mesh, arith, device, rank, world, dist, geom=0):
         "n": n_dofs, "nglobal": op.nglobal, "elements": list(dims),
     }
     if arith != pkg.ARITH_FP64:
-        eb, staged = op.tile_info()
-        out["roofline"]["tile"] = {"elements_per_block": eb, "g_staged_by_bulk_copy": bool(staged)}
+        eb, sched, seq = op.tile_info()
+        out["roofline"]["tile"] = {"elements_per_block": eb,
+                                   "schedule": ["G ring (cp.async)", "G staged (bulk copy)", "pipelined sequences"][sched],
+                                   "elements_per_sequence": seq}
     op.close()
     return out
 
@@ -302,7 +310,8 @@ def run_ours(args):
     N, K, W = args.order, args.steps, max(3, args.warmup)
     mesh = make_mesh(pkg, N, args.k)
     head_arith = pkg.ARITH_DF64 if args.arith == "df64" else pkg.ARITH_FP64
-    head = measure(pkg, args, mesh, head_arith, device, rank, world, dist)
+    head_geom = pkg.GEOM_RECOMPUTE if args.geom == "recompute" else pkg.GEOM_STORED
+    head = measure(pkg, args, mesh, head_arith, device, rank, world, dist, geom=head_geom)
     variants = {}
     if not args.headline_only:
         other = pkg.ARITH_FP64 if head_arith == pkg.ARITH_DF64 else pkg.ARITH_DF64

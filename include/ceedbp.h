@@ -282,10 +282,23 @@ ceedbp_status ceedbp_batch_destroy(ceedbp_batch* batch);
 const char* ceedbp_batch_last_error(const ceedbp_batch* batch);
 
 /* Shape the setup autotuner chose for the FP32-pair element kernel
- * (CEEDBP_ARITH_DF64): elements per thread block and whether G is staged in
- * shared memory by a bulk asynchronous copy (1) or prefetched into registers (0).
- * Both outputs are 0 for contexts without the pair path. */
-ceedbp_status ceedbp_tile_info(const ceedbp_ctx* ctx, int* elems_per_block, int* staged);
+ * (CEEDBP_ARITH_DF64): elements in flight per thread block, the schedule
+ * (0: G fetched two slabs ahead into a ring by per-thread asynchronous copies;
+ * 1: the element's G staged in shared memory by one bulk asynchronous copy;
+ * 2: software-pipelined sequences, each group of p1^2 threads working through
+ * `seq` consecutive elements while fetching the next one's data), and seq
+ * (1 for schedules 0 and 1).  Outputs are 0 (seq 1) for contexts without the
+ * pair path; any output pointer may be NULL. */
+ceedbp_status ceedbp_tile_info(const ceedbp_ctx* ctx, int* elems_per_block, int* schedule, int* seq);
+
+/* Replace the autotuner's choice by one of the shapes it times (same meaning
+ * as ceedbp_tile_info; seq is ignored for schedules 0 and 1).  Every shape
+ * computes the same element results; the fused (p, A p) may differ in the last
+ * bits because the summation order of the block partials changes.  Returns
+ * CEEDBP_EINVAL for a shape that is not launchable at this order,
+ * CEEDBP_EUNSUPPORTED on a context without the pair path.  Synchronises the
+ * context's stream and drops its captured CUDA graphs. */
+ceedbp_status ceedbp_set_tile(ceedbp_ctx* ctx, int elems_per_block, int schedule, int seq);
 
 /* Release every resource owned by ctx (NULL is accepted). */
 ceedbp_status ceedbp_destroy(ceedbp_ctx* ctx);

@@ -70,7 +70,9 @@ _SIGS = {
     "ceedbp_solve": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo)]),
     "ceedbp_apply_noalloc": (ctypes.c_int, [_P, _P, _P, _P]),
     "ceedbp_destroy": (ctypes.c_int, [_P]),
-    "ceedbp_tile_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "ceedbp_tile_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_int)]),
+    "ceedbp_set_tile": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "ceedbp_batch_setup": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(Params), ctypes.POINTER(_P),
                                           ctypes.POINTER(_P), ctypes.POINTER(_P), _P, ctypes.POINTER(_P)]),
     "ceedbp_batch_solve": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(SolveOpts),
@@ -258,10 +260,16 @@ class Operator:
         return g
 
     def tile_info(self):
-        """(elements per block, G staged) chosen by the setup autotuner for the pair kernel."""
-        eb, st = ctypes.c_int(0), ctypes.c_int(0)
-        _check(self.lib.ceedbp_tile_info(self.ctx, ctypes.byref(eb), ctypes.byref(st)), self.ctx)
-        return eb.value, st.value
+        """(elements per block, schedule, elements per sequence) chosen by the setup autotuner for the
+        pair kernel; schedule 0 = G ring, 1 = G staged by a bulk copy, 2 = pipelined sequences."""
+        eb, st, seq = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        _check(self.lib.ceedbp_tile_info(self.ctx, ctypes.byref(eb), ctypes.byref(st), ctypes.byref(seq)),
+               self.ctx)
+        return eb.value, st.value, seq.value
+
+    def set_tile(self, elems_per_block: int, schedule: int, seq: int = 1):
+        """Pin the pair kernel's shape to one the autotuner times (see tile_info)."""
+        _check(self.lib.ceedbp_set_tile(self.ctx, elems_per_block, schedule, seq), self.ctx)
 
     def prepare_mixed(self, precision: int):
         _check(self._call(self.lib.ceedbp_prepare_mixed, precision), self.ctx)

@@ -317,14 +317,15 @@ ceedbp_status setup_impl(ceedbp_ctx* c, const double* coords, const int64_t* l2g
     a.fault = &c->d_state->fault;
     CK(c, cudaStreamSynchronize(s));
     // autotuner: elements per block and G staging of the pair kernel, timed on this mesh
-    int cand_eb[16], cand_st[16];
-    const int ncand = elem_df_tile_candidates(m, cand_eb, cand_st, 16);
+    int cand_eb[32], cand_st[32], cand_ns[32];
+    const int ncand = elem_df_tile_candidates(m, cand_eb, cand_st, cand_ns, 32, !c->no_pipeline);
     if (ncand == 0) return fail(c, CEEDBP_EUNSUPPORTED, "no launchable shape for the pair kernel at this order");
     float best = 1e30f;
     int best_k = 0;
     for (int k = 0; k < ncand && ncand > 1; ++k) {
       m.tune_eb = cand_eb[k];
       m.tune_stage = cand_st[k];
+      m.tune_ns = cand_ns[k];
       CK(c, launch_elem_df(m, a, s));  // warm-up of this shape
       CK(c, cudaEventRecord(c->ev0, s));
       for (int r = 0; r < 3; ++r) CK(c, launch_elem_df(m, a, s));
@@ -339,6 +340,7 @@ ceedbp_status setup_impl(ceedbp_ctx* c, const double* coords, const int64_t* l2g
     }
     m.tune_eb = cand_eb[best_k];
     m.tune_stage = cand_st[best_k];
+    m.tune_ns = cand_ns[best_k];
     CK(c, launch_elem_df(m, a, s));  // the chosen shape, launched once outside any capture
     CK(c, cudaStreamSynchronize(s));
     CK(c, cudaMemsetAsync(&c->d_state->fault, 0, sizeof(int), s));
@@ -822,11 +824,37 @@ ceedbp_status ceedbp_kappa_gradient(ceedbp_ctx* c, const double* u, const double
   return CEEDBP_OK;
 }
 
-ceedbp_status ceedbp_tile_info(const ceedbp_ctx* c, int* eb, int* staged) {
+ceedbp_status ceedbp_tile_info(const ceedbp_ctx* c, int* eb, int* staged, int* seq) {
   if (!c) return CEEDBP_EINVAL;
   const bool df = c->arith == CEEDBP_ARITH_DF64;
   if (eb) *eb = df ? c->mesh.tune_eb : 0;
   if (staged) *staged = df ? c->mesh.tune_stage : 0;
+  if (seq) *seq = df && c->mesh.tune_stage == 2 ? c->mesh.tune_ns : 1;
+  return CEEDBP_OK;
+}
+
+ceedbp_status ceedbp_set_tile(ceedbp_ctx* c, int eb, int schedule, int seq) {
+  if (!c) return fail(c, CEEDBP_EINVAL, "null context");
+  if (c->arith != CEEDBP_ARITH_DF64) return fail(c, CEEDBP_EUNSUPPORTED, "tile shapes belong to the pair path");
+  int cand_eb[32], cand_st[32], cand_ns[32];
+  const int ncand = elem_df_tile_candidates(c->mesh, cand_eb, cand_st, cand_ns, 32, !c->no_pipeline);
+  int hit = -1;
+  for (int k = 0; k < ncand; ++k)
+    if (cand_eb[k] == eb && cand_st[k] == schedule && (schedule != 2 || cand_ns[k] == seq)) hit = k;
+  if (hit < 0) return fail(c, CEEDBP_EINVAL, "not a launchable shape of the pair kernel at this order");
+  cudaStream_t s = c->stream;
+  CK(c, cudaStreamSynchronize(s));
+  // captured iterations hold the previous shape
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+  c->graphs.clear();
+  c->mesh.tune_eb = cand_eb[hit];
+  c->mesh.tune_stage = cand_st[hit];
+  c->mesh.tune_ns = cand_ns[hit];
+  ElemDfArgs a = df_args(c);
+  a.u_f64 = c->d_r;
+  a.mask_in = 1;
+  CK(c, launch_elem_df(c->mesh, a, s));  // one launch outside any capture (attribute setup)
+  CK(c, cudaStreamSynchronize(s));
   return CEEDBP_OK;
 }
 

@@ -38,6 +38,7 @@ struct ceedbp_ctx {
   // Jacobi inverse; the CG pair vectors reuse d_r, d_p, d_ax and the local
   // scratch d_wl (a pair has the size of a double).
   int arith = 0;
+  bool no_pipeline = false;  // batched groups: the pipelined pair schedule has no per-problem block tables
   ceedbp::dfloat* d_Gdf = nullptr;
   ceedbp::dfloat* d_Ddf = nullptr;
   ceedbp::dfloat* d_dinvdf = nullptr;

@@ -78,7 +78,9 @@ struct DeviceMesh {
   const int* slots;     // [E p1^3] local slots sorted by node, then slot
   const double* basis;  // device 1D tables (layout above)
   int tune_eb;          // elements per block of the FP32-pair kernel (0 = default; set by the autotuner)
-  int tune_stage;       // 1: stage G in shared memory with a bulk copy (autotuner), 0: register prefetch
+  int tune_stage;       // pair kernel schedule (autotuner): 0 G ring by cp.async, 1 G staged by a bulk
+                        // copy, 2 software-pipelined element sequences (elem_dfp_kernel)
+  int tune_ns;          // elements per slot sequence of the pipelined schedule
   const double* X;      // [E][3][p1^3] nodal coordinates when the factors are recomputed, else nullptr
 };
 
@@ -133,7 +135,7 @@ cudaError_t launch_pcg_dir(const DeviceMesh& m, const double* r, double* p, cons
 struct dfloat;
 struct ElemDfArgs;
 int elem_df_blocks(const DeviceMesh& m);
-int elem_df_tile_candidates(const DeviceMesh& m, int* eb, int* stage, int cap);
+int elem_df_tile_candidates(const DeviceMesh& m, int* eb, int* stage, int* ns, int cap, bool pipelined);
 cudaError_t set_df_dconst(int p1, const dfloat* host, cudaStream_t s);
 cudaError_t launch_elem_df(const DeviceMesh& m, const ElemDfArgs& a, cudaStream_t s);
 cudaError_t launch_init_df(const DeviceMesh& m, const double* b, const double* ax, double* x, dfloat* xd, dfloat* r,

@@ -113,3 +113,54 @@ def test_df64_sampled_rows_largest_n7():
     got = w[torch.from_numpy(nodes).cuda()].cpu().numpy()
     assert np.max(np.abs(got - rows)) <= APPLY_TOL * 10 * np.max(np.abs(rows))
     op.close()
+
+
+PIPELINED = [(1, 4), (1, 8), (1, 16), (2, 4), (2, 16)]
+
+
+@pytest.mark.parametrize("bp,N,dims", [(5, 1, (3, 2, 2)), (5, 3, (3, 2, 5)), (5, 4, (2, 3, 3)), (5, 5, (3, 3, 2)),
+                                        (5, 7, (5, 3, 3)), (6, 3, (2, 3, 2)), (6, 7, (3, 2, 2))])
+def test_pipelined_schedule_parity_and_same_bits(bp, N, dims):
+    """Every pair-kernel schedule computes the same element results: the pipelined
+    sequences (ragged last block: E is not a multiple of eb * seq) match the oracle
+    to 1e-12 and the per-element ring schedule bit for bit."""
+    op = _box(bp, dims, N)
+    ref = BakeoffProblem(bp, *dims, N, amp=0.05)
+    u = _vec(op.nglobal, op.ncomp, 13)
+    ut = torch.from_numpy(u).cuda()
+    w_ref = ref.apply(u)
+    outs = []
+    for eb, seq in PIPELINED:
+        try:
+            op.set_tile(eb, 2, seq)
+        except pkg.CeedbpError as e:
+            assert e.status == pkg.EINVAL
+            continue
+        assert op.tile_info() == (eb, 2, seq)
+        w = op.apply(ut).cpu().numpy()
+        assert _rel(w, w_ref) < APPLY_TOL
+        outs.append(w)
+    assert len(outs) >= 3
+    op.set_tile(1, 0)
+    w0 = op.apply(ut).cpu().numpy()
+    for w in outs:
+        np.testing.assert_array_equal(w, w0)
+    with pytest.raises(pkg.CeedbpError) as ei:
+        op.set_tile(3, 2, 5)
+    assert ei.value.status == pkg.EINVAL
+
+
+@pytest.mark.parametrize("bp,N,dims,tile", [(5, 7, (2, 2, 3), (1, 8)), (5, 3, (4, 3, 3), (2, 4)),
+                                             (6, 3, (2, 2, 2), (1, 4))])
+def test_pipelined_schedule_solve_parity(bp, N, dims, tile):
+    op = _box(bp, dims, N)
+    op.set_tile(tile[0], 2, tile[1])
+    ref = BakeoffProblem(bp, *dims, N, amp=0.05)
+    b = ref.rhs(_vec(op.nglobal, op.ncomp, 0))
+    x, info = op.solve(torch.from_numpy(np.ascontiguousarray(b)).cuda(), tol=1e-8)
+    _, infos = ref.solve(b, tol=1e-8)
+    for c in range(op.ncomp):
+        assert abs(info["iters"][c] - infos[c]["iters"]) <= 1
+        assert abs(info["rel_res"][c] - infos[c]["rel_res"]) <= 1e-10
+    res = np.linalg.norm(ref.apply(x.cpu().numpy()) - b) / np.linalg.norm(b)
+    assert res < 1e-7
