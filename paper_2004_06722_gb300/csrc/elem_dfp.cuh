@@ -1,7 +1,7 @@
 // Software-pipelined variant of the FP32-pair BK5/BK6 element kernel.
 //
-// Same arithmetic as elem_df_kernel (splitter accumulation, per-direction
-// transpose accumulators, fused (u, w) and alpha), different schedule: each
+// Same operator arithmetic as elem_df_kernel (splitter accumulation,
+// per-direction transpose accumulators, fused alpha), different schedule: each
 // group of p1*p1 threads (a slot) works through a sequence of `ns` elements and
 // fetches the next element's data while it computes the current one, so the
 // dependent l2g -> u gather no longer stalls the warps:
@@ -19,8 +19,14 @@
 // shared memory doubles as the pair tile of the r and s derivatives (rows of
 // p1+1 pairs, no bank conflicts between row and column reads).
 //
-// Shared memory per slot: 3-slab G ring, u tile, two l2g buffers, two
-// gradient tiles; for p1 = 8 and one component 27 KB.
+// The slab loops are not unrolled (the unrolled element body, ~75 KB of
+// code, thrashed the instruction cache); the t-direction values therefore go
+// through a private shared tile, and (p, A p) is accumulated in quadrature form
+// sum (u_r, u_s, u_t) . G (u_r, u_s, u_t) during the gradient phase, which equals
+// sum (u, w) of Algorithm 1 up to rounding.
+//
+// Shared memory per slot: 3-slab G ring, u tile, three gradient tiles, two
+// l2g buffers; for p1 = 8 and one component 31.7 KB.
 #pragma once
 
 #include "elem_df.cuh"
@@ -35,7 +41,7 @@ struct ElemDfpShape {
 };
 
 // layout: [red 32 NC doubles][smax 2 x 4 x 32 u32][sD p1 x (p1+1) pairs] then per slot:
-//         [G ring][sU NC tiles][sR NC tiles][sS NC tiles][sL 2 x p1^3 ints]
+//         [G ring][sU NC tiles][sR NC tiles][sS NC tiles][sT NC tiles][sL 2 x p1^3 ints]
 template <int P1, int NC>
 __host__ __device__ inline size_t elem_dfp_head_bytes() {
   const size_t h = sizeof(double) * 32 * NC + sizeof(unsigned) * 256 + sizeof(dfloat) * P1 * (P1 + 1);
@@ -45,7 +51,7 @@ __host__ __device__ inline size_t elem_dfp_head_bytes() {
 template <int P1, int NC>
 __host__ __device__ inline size_t elem_dfp_slot_bytes() {
   using S = ElemDfpShape<P1, NC>;
-  const size_t b = sizeof(dfloat) * (size_t(S::RING) + 3 * NC * size_t(S::TILE)) + sizeof(int) * 2 * S::P3;
+  const size_t b = sizeof(dfloat) * (size_t(S::RING) + 4 * NC * size_t(S::TILE)) + sizeof(int) * 2 * S::P3;
   return (b + 15) / 16 * 16;
 }
 
@@ -80,7 +86,8 @@ __global__ void __launch_bounds__(P1 <= 8 ? 256 : 1024, (P1 <= 8 && NC == 1) ? 2
   dfloat* sU = ring + S::RING;
   dfloat* sR = sU + NC * TILE;
   dfloat* sS = sR + NC * TILE;
-  int* sL = reinterpret_cast<int*>(sS + NC * TILE);  // [2][P3], private column entries
+  dfloat* sT = sS + NC * TILE;                        // private columns of the t components
+  int* sL = reinterpret_cast<int*>(sT + NC * TILE);  // [2][P3], private column entries
   const int my = j * ROW + i;
 
   for (int q = tid; q < PP; q += blockDim.x) sD[(q / P1) * ROW + (q % P1)] = a.D[q];
@@ -175,9 +182,14 @@ __global__ void __launch_bounds__(P1 <= 8 ? 256 : 1024, (P1 <= 8 && NC == 1) ? 2
     }
     const float sig1 = splitter(a.dnorm_row * __uint_as_float(mx_s[slot]));
 
-    // ---- gradient and geometric factors
-    dfloat wt[NC][P1];
+    // ---- gradient, geometric factors and the element energy (p^e, A^e p^e)
+    //      = sum over points of (u_r, u_s, u_t) . G (u_r, u_s, u_t), the fused dot of Algorithm 1
+    //      in quadrature form; slab loop kept rolled (a fully unrolled element body overflows the
+    //      instruction cache), so the t components live in the private tile sT
     float mr = 0.0f, ms = 0.0f, mt = 0.0f;
+    dfloat energy[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) energy[c] = dfloat{0.0f, 0.0f};
     {
       dfloat Di[P1], Dj[P1];
 #pragma unroll
@@ -186,7 +198,7 @@ __global__ void __launch_bounds__(P1 <= 8 ? 256 : 1024, (P1 <= 8 && NC == 1) ? 2
         Dj[n] = sD[j * ROW + n];
       }
       const bool next_live = live(s + 1);
-#pragma unroll
+#pragma unroll 1
       for (int k = 0; k < P1; ++k) {
         // prefetch the slab two ahead: this element's, or the next element's first two
         const int rp2 = rp + 2 >= 3 ? rp - 1 : rp + 2;
@@ -205,6 +217,7 @@ __global__ void __launch_bounds__(P1 <= 8 ? 256 : 1024, (P1 <= 8 && NC == 1) ? 2
         for (int q = 0; q < 6; ++q) g[q] = gs[q * PP];
         const float gb = fmaxf(fmaxf(row_abs_sum3(g[0], g[1], g[2]), row_abs_sum3(g[1], g[3], g[4])),
                                row_abs_sum3(g[2], g[4], g[5]));
+        const dfloat* dkrow = c_Ddf[P1 - 2] + k * P1;
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
           SplitAcc ar(sig1), as(sig1), at(sig1);
@@ -213,7 +226,7 @@ __global__ void __launch_bounds__(P1 <= 8 ? 256 : 1024, (P1 <= 8 && NC == 1) ? 2
           for (int n = 0; n < P1; ++n) {
             const dfloat xr = xs[j * ROW + n];
             const dfloat xq = xs[n * ROW + i];
-            const dfloat dk = c_Ddf[P1 - 2][k * P1 + n];
+            const dfloat dk = dkrow[n];
             ar.add(Di[n].hi, Di[n].lo, xr.hi, xr.lo);
             as.add(Dj[n].hi, Dj[n].lo, xq.hi, xq.lo);
             at.add(dk.hi, dk.lo, xc[c][n].hi, xc[c][n].lo);
@@ -234,10 +247,18 @@ __global__ void __launch_bounds__(P1 <= 8 ? 256 : 1024, (P1 <= 8 && NC == 1) ? 2
           const dfloat vr = wr.result(sg), vs = ws.result(sg), vt = wq.result(sg);
           sR[c * TILE + k * SLAB + my] = vr;
           sS[c * TILE + k * SLAB + my] = vs;
-          wt[c][k] = vt;
+          sT[c * TILE + k * SLAB + my] = vt;
           mr = fmaxf(mr, fabsf(vr.hi));
           ms = fmaxf(ms, fabsf(vs.hi));
           mt = fmaxf(mt, fabsf(vt.hi));
+          // point energy u_r v_r + u_s v_s + u_t v_t with a splitter from its own bound
+          const float eb_ = fabsf(ur.hi) * fabsf(vr.hi) + fabsf(us.hi) * fabsf(vs.hi) + fabsf(ut.hi) * fabsf(vt.hi);
+          const float se = splitter(eb_);
+          SplitAcc ep(se);
+          ep.add(ur.hi, ur.lo, vr.hi, vr.lo);
+          ep.add(us.hi, us.lo, vs.hi, vs.lo);
+          ep.add(ut.hi, ut.lo, vt.hi, vt.lo);
+          energy[c] = dw_add(energy[c], ep.result(se));
         }
       }
     }
@@ -255,7 +276,7 @@ __global__ void __launch_bounds__(P1 <= 8 ? 256 : 1024, (P1 <= 8 && NC == 1) ? 2
     const float sig_s = splitter(a.dnorm_col * __uint_as_float(mx_s[64 + slot]));
     const float sig_t = splitter(a.dnorm_col * __uint_as_float(mx_s[96 + slot]));
 
-    // ---- transpose gradient, output, fused dot
+    // ---- transpose gradient and output
     if (active) {
       dfloat Dni[P1], Dnj[P1];
 #pragma unroll
@@ -264,42 +285,40 @@ __global__ void __launch_bounds__(P1 <= 8 ? 256 : 1024, (P1 <= 8 && NC == 1) ? 2
         Dnj[n] = sD[n * ROW + j];
       }
       dfloat* wl = a.wl + size_t(elem_of(s)) * P3 * NC;
-      dfloat acc_dot[NC];
-#pragma unroll
-      for (int c = 0; c < NC; ++c) acc_dot[c] = dfloat{0.0f, 0.0f};
-#pragma unroll
+#pragma unroll 1
       for (int k = 0; k < P1; ++k) {
         const int idx = k * PP + t;
         const bool skip = a.skip_dirichlet_out && ((dmask >> k) & 1u);
+        const dfloat* dkcol = c_Ddf[P1 - 2] + k;
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
           SplitAcc acr(sig_r), acs(sig_s), act(sig_t);
           const dfloat* rs = sR + c * TILE + k * SLAB;
           const dfloat* ss = sS + c * TILE + k * SLAB;
+          const dfloat* ts = sT + c * TILE + my;
 #pragma unroll
           for (int n = 0; n < P1; ++n) {
             const dfloat vr = rs[j * ROW + n];
             const dfloat vs = ss[n * ROW + i];
-            const dfloat dk = c_Ddf[P1 - 2][n * P1 + k];
+            const dfloat vt = ts[n * SLAB];
+            const dfloat dk = dkcol[n * P1];
             acr.add(Dni[n].hi, Dni[n].lo, vr.hi, vr.lo);
             acs.add(Dnj[n].hi, Dnj[n].lo, vs.hi, vs.lo);
-            act.add(dk.hi, dk.lo, wt[c][n].hi, wt[c][n].lo);
+            act.add(dk.hi, dk.lo, vt.hi, vt.lo);
           }
-          const dfloat w = dw_add(dw_add(acr.result(sig_r), acs.result(sig_s)), act.result(sig_t));
           if (!skip) {
+            const dfloat w = dw_add(dw_add(acr.result(sig_r), acs.result(sig_s)), act.result(sig_t));
             dfloat wn;
             two_sum(w.hi, w.lo, wn.hi, wn.lo);
             wl[size_t(idx) * NC + c] = wn;
           }
-          acc_dot[c] = dw_add(acc_dot[c], dw_mul(w, xc[c][k]));
         }
       }
 #pragma unroll
-      for (int c = 0; c < NC; ++c) dot[c] += df_to_f64(acc_dot[c]);
+      for (int c = 0; c < NC; ++c) dot[c] += df_to_f64(energy[c]);
     }
-    // the next entry's gather writes the u tile and the gradient tiles are
-    // rewritten after its barrier; the barrier after this entry's gradient
-    // already ordered every read of the u tile before the copies above
+    // the next entry's gather rewrites the u tile only after its own copies land, and the
+    // gradient tiles only after its first barrier, by which time every thread is done here
   }
   cp_async_wait_all();
 
