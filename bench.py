@@ -52,7 +52,7 @@ def parse_args():
                     help="geometric factors of the headline arm: stored, or recomputed in the element kernel")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-k", type=int, default=9, help="E = 2^k elements for the oracle sample")
-    ap.add_argument("--workload", choices=["sweep", "batched", "mixed", "adjoint", "bp-sweep"], default="sweep",
+    ap.add_argument("--workload", choices=["sweep", "batched", "mixed", "adjoint", "bp-sweep", "bk-sweep"], default="sweep",
                     help="sweep: BP5 n-sweep headline; batched: 256 BP5 problems batched vs one at a time; "
                          "mixed: BP6 defect correction vs FP64 PCG; adjoint: dJ/dkappa pipeline")
     return ap.parse_args()
@@ -629,10 +629,69 @@ def run_bp_sweep(args):
                       "unit": "DOFs/s", "iters": iters, "results": out}), flush=True)
 
 
+def run_bk_sweep(args):
+    """Unassembled BK5 (BP5 element operator, no Q, Q^T or mask; ceedbp_bk_apply) at N in {1, 2, 3, 5, 7,
+    9, 11, 15}, FP64 and FP32 pairs, on E = 2^k boxes with n = E N^3 from ~1e3 to ~1e8 (k in steps of 2):
+    time per apply (CUDA events over `--sweep-iters` applies after 3 warm-ups), algorithmic GFLOP/s
+    (12 p1^4 + 15 p1^3 per element), DOFs/s and r_max, n_0.8 per (arith, N)."""
+    import numpy as np
+    import torch
+
+    import paper_2004_06722_gb300 as pkg
+    from synth import box_dims, uniform_pm1
+    reps = args.sweep_iters
+    out = {}
+    for name, arith in (("fp64", pkg.ARITH_FP64), ("df64", pkg.ARITH_DF64)):
+        for N in (1, 2, 3, 5, 7, 9, 11, 15):
+            p1 = N + 1
+            ns, rates, gflops, tpp = [], [], [], []
+            k = 0
+            while 2 ** k * N ** 3 < 1e3:
+                k += 1
+            while 2 ** k * N ** 3 <= 1.2e8:
+                dims = box_dims(k)
+                E = dims[0] * dims[1] * dims[2]
+                coords, l2g, dirichlet = pkg.mesh_box(*dims, N, 0.05)
+                op = pkg.Operator(5, N, coords, l2g, dirichlet, arith=arith)
+                del coords, l2g
+                uL = torch.from_numpy(uniform_pm1(0, np.arange(E * p1 ** 3)).reshape(E, p1 ** 3)).cuda()
+                wL = torch.empty_like(uL)
+                for _ in range(3):
+                    op.bk_apply(uL, wL)
+                ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                with torch.cuda.stream(op.stream):
+                    torch.cuda.synchronize()
+                    ev0.record(op.stream)
+                    for _ in range(reps):
+                        op.bk_apply(uL, wL)
+                    ev1.record(op.stream)
+                torch.cuda.synchronize()
+                t = ev0.elapsed_time(ev1) * 1e-3 / reps
+                n = E * N ** 3
+                ns.append(n)
+                rates.append(n / t)
+                gflops.append(E * (12 * p1 ** 4 + 15 * p1 ** 3) / t / 1e9)
+                tpp.append(t / n)
+                op.close()
+                del uL, wL
+                torch.cuda.empty_cache()
+                k += 2
+            rmax = max(rates)
+            n80 = n_08(ns, rates)
+            out[f"{name}_N{N}"] = {"n": ns, "dofs_per_s": rates, "gflops": gflops, "s_per_dof": tpp,
+                                   "r_max": rmax, "n_0.8": n80, "gflops_max": max(gflops)}
+            print(json.dumps({f"{name}_N{N}": {"r_max": rmax, "n_0.8": n80, "gflops_max": max(gflops)}}),
+                  file=sys.stderr, flush=True)
+    print(json.dumps({"metric": "unassembled BK5 apply: DOFs/s and GFLOP/s vs n (FP64 and FP32 pairs)",
+                      "unit": "DOFs/s", "reps": reps, "results": out}), flush=True)
+
+
 def main():
     args = parse_args()
     if args.workload == "bp-sweep":
         return run_bp_sweep(args)
+    if args.workload == "bk-sweep":
+        return run_bk_sweep(args)
     if args.workload == "batched":
         return run_batched(args)
     if args.workload == "mixed":

@@ -281,6 +281,33 @@ ceedbp_status ceedbp_batch_solve(ceedbp_batch* batch, const double* const* b_dev
 ceedbp_status ceedbp_batch_destroy(ceedbp_batch* batch);
 const char* ceedbp_batch_last_error(const ceedbp_batch* batch);
 
+/*
+ * Helmholtz operator H = A + beta B of Eq. (17) (the equation of Eq. (4) with
+ * constant mu = 1 (or kappa) and beta): after this call ceedbp_apply,
+ * ceedbp_apply_noalloc, ceedbp_bk_apply and ceedbp_solve use A + beta B,
+ * with B the mass matrix in the BP's own quadrature (Eq. (34)), the same
+ * Dirichlet mask, and the Jacobi diagonal of A + beta B.  beta = 0 restores
+ * the plain stiffness.  Built for BP3-BP6 with CEEDBP_ARITH_FP64 and stored
+ * factors (CEEDBP_EUNSUPPORTED otherwise, and for contexts prepared for
+ * defect correction); beta must be finite and >= 0 (CEEDBP_EINVAL).
+ * Synchronises the stream and drops the context's captured graphs.
+ */
+ceedbp_status ceedbp_set_helmholtz(ceedbp_ctx* ctx, double beta);
+
+/*
+ * Unassembled element operator (the "BK" kernels of Table 1): for every
+ * element e, w^e = A^e u^e (BP3-BP6: the stiffness of Eq. (22), or Eqs.
+ * (31)-(33) with GL quadrature; no Dirichlet mask) or w^e = B^e u^e (BP1,
+ * BP2: Eq. (34)), without Q or Q^T.
+ *   uL, wL  device [E][p1^3][ncomp] FP64, element-local values (the layout of
+ *           coords); must not overlap.
+ * With CEEDBP_ARITH_DF64 the pair kernel computes w^e and an extra pass turns
+ * the pairs into FP64.  The first call allocates an identity gather map of
+ * E p1^3 int32 (kept until destroy); later calls allocate nothing.  Stream
+ * ordered on the context's stream; returns without synchronising.
+ */
+ceedbp_status ceedbp_bk_apply(ceedbp_ctx* ctx, const double* uL, double* wL);
+
 /* Shape the setup autotuner chose for the FP32-pair element kernel
  * (CEEDBP_ARITH_DF64): elements in flight per thread block, the schedule
  * (0: G fetched two slabs ahead into a ring by per-thread asynchronous copies;

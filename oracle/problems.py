@@ -32,7 +32,7 @@ from .quadrature import bp_rule
 
 class BakeoffProblem:
     def __init__(self, bp: int, Ex: int, Ey: int, Ez: int, N: int, amp: float = 0.05,
-                 kappa: np.ndarray | None = None, rule=None):
+                 kappa: np.ndarray | None = None, rule=None, beta: float = 0.0):
         if bp not in (1, 2, 3, 4, 5, 6):
             raise ValueError("bake-off problems are BP1..BP6")
         self.bp, self.N = bp, N
@@ -54,6 +54,11 @@ class BakeoffProblem:
                 Ae.append(m["A"])
         self.B = assemble(self.l2g, Be, self.n_global)
         self.A = self.B if mass_only else assemble(self.l2g, Ae, self.n_global)
+        if beta != 0.0:
+            if mass_only:
+                raise ValueError("the Helmholtz term applies to BP3-BP6")
+            # H = A + beta B, Eq. (17): the Galerkin form of Eq. (4) with constant beta
+            self.A = (self.A + beta * self.B).tocsr()
         if mass_only:
             self.free = np.ones(self.n_global, dtype=bool)
         else:

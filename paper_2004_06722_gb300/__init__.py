@@ -72,6 +72,8 @@ _SIGS = {
     "ceedbp_destroy": (ctypes.c_int, [_P]),
     "ceedbp_tile_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_int)]),
+    "ceedbp_bk_apply": (ctypes.c_int, [_P, _P, _P]),
+    "ceedbp_set_helmholtz": (ctypes.c_int, [_P, ctypes.c_double]),
     "ceedbp_set_tile": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "ceedbp_batch_setup": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(Params), ctypes.POINTER(_P),
                                           ctypes.POINTER(_P), ctypes.POINTER(_P), _P, ctypes.POINTER(_P)]),
@@ -216,6 +218,21 @@ class Operator:
         _check(st, self.ctx)
         return w
 
+    def bk_apply(self, uL, out=None):
+        """ceedbp_bk_apply: element-local w^e = A^e u^e (or B^e u^e), uL of shape [E, p1^3] or
+        [E, p1^3, 3]; no gather-scatter, no Dirichlet mask."""
+        import torch
+        p3 = (self.order + 1) ** 3
+        shape = (self.nelem, p3) if self.ncomp == 1 else (self.nelem, p3, 3)
+        if not (uL.is_cuda and uL.dtype == torch.float64 and uL.is_contiguous()) or tuple(uL.shape) != shape:
+            raise ValueError(f"uL must be a contiguous float64 CUDA tensor of shape {shape}")
+        w = torch.empty(shape, dtype=torch.float64, device=self.device) if out is None else out
+        if tuple(w.shape) != shape or not w.is_contiguous() or w.dtype != torch.float64:
+            raise ValueError(f"out must be a contiguous float64 CUDA tensor of shape {shape}")
+        _check(self._call(self.lib.ceedbp_bk_apply, ctypes.c_void_p(uL.data_ptr()), ctypes.c_void_p(w.data_ptr())),
+               self.ctx)
+        return w
+
     def mass(self, u, out=None):
         w = self.empty() if out is None else out
         _check(self._call(self.lib.ceedbp_mass, self._vec(u), self._vec(w)), self.ctx)
@@ -266,6 +283,10 @@ class Operator:
         _check(self.lib.ceedbp_tile_info(self.ctx, ctypes.byref(eb), ctypes.byref(st), ctypes.byref(seq)),
                self.ctx)
         return eb.value, st.value, seq.value
+
+    def set_helmholtz(self, beta: float):
+        """Use H = A + beta B (Eq. (17)) in apply, bk_apply and solve; beta = 0 restores A."""
+        _check(self._call(self.lib.ceedbp_set_helmholtz, ctypes.c_double(beta)), self.ctx)
 
     def set_tile(self, elems_per_block: int, schedule: int, seq: int = 1):
         """Pin the pair kernel's shape to one the autotuner times (see tile_info)."""

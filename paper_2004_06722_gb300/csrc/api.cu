@@ -86,7 +86,7 @@ void release(ceedbp_ctx* c) {
   void* ptrs[] = {c->d_l2g, c->d_off, c->d_slots, c->d_basis, c->d_G, c->d_Mq, c->d_dinv, c->d_mdiag,
                   c->d_wl, c->d_r, c->d_p, c->d_ax, c->d_part_apply, c->d_part_vec, c->d_state,
                   c->d_Gdf, c->d_Ddf, c->d_dinvdf, c->d_G32, c->d_Gbf, c->d_dinv32, c->d_xin,
-                  c->d_rin, c->d_pin, c->d_outer, c->d_Ghat, c->d_scal, c->d_X};
+                  c->d_rin, c->d_pin, c->d_outer, c->d_Ghat, c->d_scal, c->d_X, c->d_l2g_id};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_outer) cudaFreeHost(c->h_outer);
@@ -361,6 +361,14 @@ void release_context(ceedbp_ctx* c) { release(c); }
 
 namespace {
 
+// Helmholtz term beta B u of Eq. (17) for the stiffness kernels (beta = 0: none)
+void set_helmholtz_args(const ceedbp_ctx* c, ElemArgs& a) {
+  if (c->op_kind == kStiff && c->beta != 0.0) {
+    a.Mq = c->d_Mq;
+    a.beta = c->beta;
+  }
+}
+
 ElemDfArgs df_args(ceedbp_ctx* c) {
   ElemDfArgs a{};
   a.fault = &c->d_state->fault;
@@ -400,6 +408,7 @@ void run_iterations(ceedbp_ctx* c, double* x, int n, bool profile = false, bool 
   a.u = c->d_p;
   a.wl = c->d_wl;
   a.G = c->op_kind == kStiff ? c->d_G : c->d_Mq;
+  set_helmholtz_args(c, a);
   a.partials = c->d_part_apply;
   a.state = c->d_state;
   a.mask_in = 0;  // p is zero on Dirichlet nodes
@@ -580,6 +589,7 @@ ceedbp_status ceedbp_prepare_mixed(ceedbp_ctx* c, int precision) {
     return fail(c, CEEDBP_EINVAL, "precision must be CEEDBP_MIXED_FP32 or CEEDBP_MIXED_BF16");
   if (!c->colloc) return fail(c, CEEDBP_EUNSUPPORTED, "defect correction is built for BP5 and BP6");
   if (c->d_X) return fail(c, CEEDBP_EUNSUPPORTED, "this call needs stored geometric factors (geom = STORED)");
+  if (c->beta != 0.0) return fail(c, CEEDBP_EUNSUPPORTED, "defect correction is built for beta = 0");
   const int64_t n = c->prm.nglobal, nc = c->ncomp;
   const int64_t ng = c->prm.nelem * 6 * int64_t(c->q) * c->q * c->q;
   cudaStream_t s = c->stream;
@@ -645,6 +655,7 @@ ceedbp_status ceedbp_apply(ceedbp_ctx* c, const double* u, double* w) {
   a.u = u;
   a.wl = c->d_wl;
   a.G = c->op_kind == kStiff ? c->d_G : c->d_Mq;
+  set_helmholtz_args(c, a);
   a.mask_in = c->prm.bp != 1 && c->prm.bp != 2;
   a.skip_dirichlet_out = 1;
   CK(c, launch_elem(c->mesh, c->op_kind, a, c->stream));
@@ -800,6 +811,7 @@ ceedbp_status ceedbp_set_kappa(ceedbp_ctx* c, const double* kappa) {
   if (c->d_G32) CK(c, launch_narrow(c->d_G, c->d_G32, int64_t(ng), 0, s));
   if (c->d_Gbf) CK(c, launch_narrow(c->d_G, c->d_Gbf, int64_t(ng), 1, s));
   if (c->d_dinv32) CK(c, launch_narrow(c->d_dinv, c->d_dinv32, c->prm.nglobal, 0, s));
+  if (c->beta != 0.0) return ceedbp_set_helmholtz(c, c->beta);  // Jacobi of A(kappa) + beta B
   return CEEDBP_OK;
 }
 
@@ -830,6 +842,80 @@ ceedbp_status ceedbp_tile_info(const ceedbp_ctx* c, int* eb, int* staged, int* s
   if (eb) *eb = df ? c->mesh.tune_eb : 0;
   if (staged) *staged = df ? c->mesh.tune_stage : 0;
   if (seq) *seq = df && c->mesh.tune_stage == 2 ? c->mesh.tune_ns : 1;
+  return CEEDBP_OK;
+}
+
+namespace {
+__global__ void helm_diag_kernel(const double* __restrict__ dA, const double* __restrict__ dB, double beta,
+                                 double* __restrict__ out, int64_t n) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    out[i] = dA[i] + beta * dB[i];
+}
+
+__global__ void iota_kernel(int* v, int64_t n) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    v[i] = int(i);
+}
+}  // namespace
+
+ceedbp_status ceedbp_set_helmholtz(ceedbp_ctx* c, double beta) {
+  if (!c) return fail(c, CEEDBP_EINVAL, "null context");
+  if (!(beta >= 0.0) || !std::isfinite(beta)) return fail(c, CEEDBP_EINVAL, "beta must be finite and >= 0");
+  if (c->op_kind != kStiff) return fail(c, CEEDBP_EUNSUPPORTED, "the Helmholtz term applies to BP3-BP6");
+  if (c->arith != CEEDBP_ARITH_FP64 || c->d_G32 || c->d_Gbf)
+    return fail(c, CEEDBP_EUNSUPPORTED, "the Helmholtz term is built for the FP64 arithmetic without defect correction");
+  cudaStream_t s = c->stream;
+  CK(c, cudaStreamSynchronize(s));
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);  // captured launches hold the old beta
+  c->graphs.clear();
+  c->beta = beta;
+  // Jacobi diagonal of A + beta B: assembled diagonals of both, combined, inverted
+  const DeviceMesh& m = c->mesh;
+  DeviceMesh m1 = m;
+  m1.ncomp = 1;
+  const int64_t n = c->prm.nglobal;
+  const double* G = c->d_G;
+  if (!G && c->d_X) return fail(c, CEEDBP_EUNSUPPORTED, "the Helmholtz term needs stored geometric factors");
+  CK(c, launch_local_diag(m, kStiff, G, c->d_Mq, c->d_wl, s));
+  CK(c, launch_gs(m1, c->d_wl, c->d_r, 0, s));
+  CK(c, launch_local_diag(m1, kMass, nullptr, c->d_Mq, c->d_wl, s));
+  CK(c, launch_gs(m1, c->d_wl, c->d_ax, 0, s));
+  helm_diag_kernel<<<1216, 256, 0, s>>>(c->d_r, c->d_ax, beta, c->d_r, n);
+  CK(c, cudaGetLastError());
+  CK(c, launch_dinv(c->d_off, c->d_r, c->d_dinv, n, s));
+  CK(c, cudaStreamSynchronize(s));
+  return CEEDBP_OK;
+}
+
+ceedbp_status ceedbp_bk_apply(ceedbp_ctx* c, const double* uL, double* wL) {
+  if (!c || !uL || !wL) return fail(c, CEEDBP_EINVAL, "null argument");
+  cudaStream_t s = c->stream;
+  const int64_t nloc = c->prm.nelem * int64_t(c->p1) * c->p1 * c->p1;
+  if (!c->d_l2g_id) {
+    // the element kernels gather through l2g; the identity map makes them read u_L directly
+    CK(c, dalloc(&c->d_l2g_id, nloc));
+    iota_kernel<<<1216, 256, 0, s>>>(c->d_l2g_id, nloc);
+    CK(c, cudaGetLastError());
+  }
+  DeviceMesh mb = c->mesh;
+  mb.l2g = c->d_l2g_id;
+  if (c->arith == CEEDBP_ARITH_DF64) {
+    ElemDfArgs a = df_args(c);
+    a.u_f64 = uL;
+    a.mask_in = 0;
+    a.skip_dirichlet_out = 0;
+    CK(c, launch_elem_df(mb, a, s));
+    CK(c, launch_df_to_f64(reinterpret_cast<const dfloat*>(c->d_wl), wL, nloc * c->ncomp, s));
+    return CEEDBP_OK;
+  }
+  ElemArgs a{};
+  a.u = uL;
+  a.wl = wL;
+  a.G = c->op_kind == kStiff ? c->d_G : c->d_Mq;
+  set_helmholtz_args(c, a);
+  a.mask_in = 0;
+  a.skip_dirichlet_out = 0;
+  CK(c, launch_elem(mb, c->op_kind, a, s));
   return CEEDBP_OK;
 }
 

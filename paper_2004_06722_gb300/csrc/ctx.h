@@ -27,6 +27,7 @@ struct ceedbp_ctx {
   double* d_basis = nullptr;
   double* d_G = nullptr;
   double* d_X = nullptr;  // [E][3][p1^3] coordinates when the factors are recomputed
+  int* d_l2g_id = nullptr;  // identity gather map of ceedbp_bk_apply (allocated on its first call)
   double* d_Mq = nullptr;
   double* d_dinv = nullptr;
   double* d_mdiag = nullptr;
@@ -38,6 +39,7 @@ struct ceedbp_ctx {
   // Jacobi inverse; the CG pair vectors reuse d_r, d_p, d_ax and the local
   // scratch d_wl (a pair has the size of a double).
   int arith = 0;
+  double beta = 0.0;  // Helmholtz coefficient of Eq. (17) (ceedbp_set_helmholtz)
   bool no_pipeline = false;  // batched groups: the pipelined pair schedule has no per-problem block tables
   ceedbp::dfloat* d_Gdf = nullptr;
   ceedbp::dfloat* d_Ddf = nullptr;

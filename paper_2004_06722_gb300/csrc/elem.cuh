@@ -197,6 +197,15 @@ __global__ void elem_kernel(const DeviceMesh m, const ElemArgs a, const int eb) 
           vq[c][z] = v;
         }
       }
+      if (a.beta != 0.0) {  // Helmholtz: + beta B u at the quadrature points (Eq. (17))
+        const double* M = a.Mq + e * Q3;
+#pragma unroll
+        for (int z = 0; z < Q; ++z) {
+          const double bm = a.beta * __ldg(M + z * QQ + t);
+#pragma unroll
+          for (int c = 0; c < NC; ++c) vq[c][z] += bm * uq[c][z];
+        }
+      }
     }
   }
 

@@ -1,7 +1,7 @@
 // Software-pipelined variant of the FP32-pair BK5/BK6 element kernel.
 //
-// Same operator arithmetic as elem_df_kernel (splitter accumulation,
-// per-direction transpose accumulators, fused alpha), different schedule: each
+// Same arithmetic as elem_df_kernel (splitter accumulation, per-direction
+// transpose accumulators, fused (u, w) and alpha), different schedule: each
 // group of p1*p1 threads (a slot) works through a sequence of `ns` elements and
 // fetches the next element's data while it computes the current one, so the
 // dependent l2g -> u gather no longer stalls the warps:
@@ -21,9 +21,8 @@
 //
 // The slab loops are not unrolled (the unrolled element body, ~75 KB of
 // code, thrashed the instruction cache); the t-direction values therefore go
-// through a private shared tile, and (p, A p) is accumulated in quadrature form
-// sum (u_r, u_s, u_t) . G (u_r, u_s, u_t) during the gradient phase, which equals
-// sum (u, w) of Algorithm 1 up to rounding.
+// through a private shared tile, and the fused (u, w) takes x_k from the front
+// of the column registers, shifted down once per slab.
 //
 // Shared memory per slot: 3-slab G ring, u tile, three gradient tiles, two
 // l2g buffers; for p1 = 8 and one component 31.7 KB.
@@ -182,14 +181,9 @@ __global__ void __launch_bounds__(P1 <= 8 ? 256 : 1024, (P1 <= 8 && NC == 1) ? 2
     }
     const float sig1 = splitter(a.dnorm_row * __uint_as_float(mx_s[slot]));
 
-    // ---- gradient, geometric factors and the element energy (p^e, A^e p^e)
-    //      = sum over points of (u_r, u_s, u_t) . G (u_r, u_s, u_t), the fused dot of Algorithm 1
-    //      in quadrature form; slab loop kept rolled (a fully unrolled element body overflows the
-    //      instruction cache), so the t components live in the private tile sT
+    // ---- gradient and geometric factors; slab loop kept rolled (a fully unrolled element
+    //      body overflows the instruction cache), so the t components live in the private tile sT
     float mr = 0.0f, ms = 0.0f, mt = 0.0f;
-    dfloat energy[NC];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) energy[c] = dfloat{0.0f, 0.0f};
     {
       dfloat Di[P1], Dj[P1];
 #pragma unroll
@@ -251,14 +245,6 @@ __global__ void __launch_bounds__(P1 <= 8 ? 256 : 1024, (P1 <= 8 && NC == 1) ? 2
           mr = fmaxf(mr, fabsf(vr.hi));
           ms = fmaxf(ms, fabsf(vs.hi));
           mt = fmaxf(mt, fabsf(vt.hi));
-          // point energy u_r v_r + u_s v_s + u_t v_t with a splitter from its own bound
-          const float eb_ = fabsf(ur.hi) * fabsf(vr.hi) + fabsf(us.hi) * fabsf(vs.hi) + fabsf(ut.hi) * fabsf(vt.hi);
-          const float se = splitter(eb_);
-          SplitAcc ep(se);
-          ep.add(ur.hi, ur.lo, vr.hi, vr.lo);
-          ep.add(us.hi, us.lo, vs.hi, vs.lo);
-          ep.add(ut.hi, ut.lo, vt.hi, vt.lo);
-          energy[c] = dw_add(energy[c], ep.result(se));
         }
       }
     }
@@ -276,8 +262,12 @@ __global__ void __launch_bounds__(P1 <= 8 ? 256 : 1024, (P1 <= 8 && NC == 1) ? 2
     const float sig_s = splitter(a.dnorm_col * __uint_as_float(mx_s[64 + slot]));
     const float sig_t = splitter(a.dnorm_col * __uint_as_float(mx_s[96 + slot]));
 
-    // ---- transpose gradient and output
+    // ---- transpose gradient, output and the fused (p^e, w^e) of Algorithm 1; the rolled slab
+    //      loop takes x_k from the front of the column registers and shifts the column down
     if (active) {
+      dfloat acc_dot[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) acc_dot[c] = dfloat{0.0f, 0.0f};
       dfloat Dni[P1], Dnj[P1];
 #pragma unroll
       for (int n = 0; n < P1; ++n) {
@@ -306,16 +296,19 @@ __global__ void __launch_bounds__(P1 <= 8 ? 256 : 1024, (P1 <= 8 && NC == 1) ? 2
             acs.add(Dnj[n].hi, Dnj[n].lo, vs.hi, vs.lo);
             act.add(dk.hi, dk.lo, vt.hi, vt.lo);
           }
+          const dfloat w = dw_add(dw_add(acr.result(sig_r), acs.result(sig_s)), act.result(sig_t));
           if (!skip) {
-            const dfloat w = dw_add(dw_add(acr.result(sig_r), acs.result(sig_s)), act.result(sig_t));
             dfloat wn;
             two_sum(w.hi, w.lo, wn.hi, wn.lo);
             wl[size_t(idx) * NC + c] = wn;
           }
+          acc_dot[c] = dw_add(acc_dot[c], dw_mul(w, xc[c][0]));
+#pragma unroll
+          for (int n = 0; n + 1 < P1; ++n) xc[c][n] = xc[c][n + 1];
         }
       }
 #pragma unroll
-      for (int c = 0; c < NC; ++c) dot[c] += df_to_f64(energy[c]);
+      for (int c = 0; c < NC; ++c) dot[c] += df_to_f64(acc_dot[c]);
     }
     // the next entry's gather rewrites the u tile only after its own copies land, and the
     // gradient tiles only after its first barrier, by which time every thread is done here

@@ -285,6 +285,7 @@ __global__ void elem_eo_kernel(const DeviceMesh m, const ElemArgs a, const int e
 #pragma unroll
       for (int c8 = 0; c8 < 8; ++c8) {
         const int node = eo_node<P1>(i, j, k, c8 & 1, (c8 >> 1) & 1, c8 >> 2);
+        if (a.beta != 0.0) w[c8] += a.beta * __ldg(a.Mq + e * P3 + node) * u[c][c8];  // Eq. (17)
         if (!(a.skip_dirichlet_out && ((dmask >> c8) & 1))) wl[size_t(node) * NC + c] = w[c8];
         dot[c] += w[c8] * u[c][c8];
       }

@@ -156,6 +156,7 @@ __global__ void elem_rc_kernel(const DeviceMesh m, const ElemArgs a, const int e
           v += sD[n * P1 + ty] * sS[c * P3 + z * PP + n * P1 + tx];
           v += sD[n * P1 + z] * tq[c][n];
         }
+        if (a.beta != 0.0) v += a.beta * __ldg(a.Mq + e * P3 + idx) * uq[c][z];  // Eq. (17)
         if (!skip) wl[size_t(idx) * NC + c] = v;
         dot[c] += v * uq[c][z];
       }

@@ -106,6 +106,8 @@ struct ElemArgs {
   SolveState* state;     // for the fused last-block reduction (alpha) or nullptr
   int mask_in;
   int skip_dirichlet_out;
+  const double* Mq;      // Helmholtz term of Eq. (17): w += beta B u with the mass factors Mq ...
+  double beta;           // ... when beta != 0 (stiffness kernels in FP64 only)
 };
 int elem_blocks(const DeviceMesh& m);
 cudaError_t launch_elem(const DeviceMesh& m, int kind, const ElemArgs& a, cudaStream_t s);

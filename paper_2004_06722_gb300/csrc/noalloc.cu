@@ -72,6 +72,10 @@ extern "C" ceedbp_status ceedbp_apply_noalloc(const ceedbp_ctx* ctx, const doubl
   a.wl = scratch;
   a.G = ctx->op_kind == kStiff ? ctx->d_G : ctx->d_Mq;
   a.mask_in = ctx->prm.bp != 1 && ctx->prm.bp != 2;
+  if (ctx->op_kind == kStiff && ctx->beta != 0.0) {
+    a.Mq = ctx->d_Mq;
+    a.beta = ctx->beta;
+  }
   a.skip_dirichlet_out = 1;  // the masked gather-scatter never reads the skipped slots
   if (launch_elem(m, ctx->op_kind, a, s) != cudaSuccess) return CEEDBP_ECUDA;
   if (launch_gs(m, scratch, w_dev, 1, s) != cudaSuccess) return CEEDBP_ECUDA;

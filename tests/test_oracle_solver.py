@@ -133,3 +133,25 @@ def _solve_at(kappa, b, u_star, dims, N):
     p = BakeoffProblem(5, *dims, N, amp=0.05, kappa=kappa)
     u, _ = p.solve(b, tol=1e-15, maxit=5000)
     return p, u, u_star
+
+
+@pytest.mark.parametrize("bp", [3, 5, 6])
+def test_helmholtz_constant_mode_and_manufactured_solution(bp):
+    """H = A + beta B (Eq. (17)): A 1 = 0 on the unmasked matrix, so 1^T H 1 = beta |Omega| = beta;
+    and for u = sin(pi x) sin(pi y) sin(pi z), -Lap u + beta u = (3 pi^2 + beta) u, so the discrete
+    solution with that forcing approaches u (a dropped or mis-scaled beta term misses it by ~beta / 3 pi^2)."""
+    beta = 7.5
+    prob = BakeoffProblem(bp, 2, 2, 2, 5, amp=0.05, beta=beta)
+    one = np.ones(prob.n_global)
+    assert abs(one @ (prob.A @ one) - beta) < 1e-11
+    X = prob.node_coords()
+    s = np.sin(np.pi * X[:, 0]) * np.sin(np.pi * X[:, 1]) * np.sin(np.pi * X[:, 2])
+    f = (3 * np.pi ** 2 + beta) * s
+    if prob.ncomp == 3:
+        f = np.repeat(f[:, None], 3, axis=1)
+        s = np.repeat(s[:, None], 3, axis=1)
+    x, infos = prob.solve(prob.rhs(f), tol=1e-12)
+    assert all(i["converged"] for i in infos)
+    assert np.max(np.abs(x - s)) < 2e-3
+    with pytest.raises(ValueError):
+        BakeoffProblem(1, 1, 1, 1, 2, beta=1.0)
