@@ -631,7 +631,7 @@ def run_bp_sweep(args):
 
 def run_bk_sweep(args):
     """Unassembled BK5 (BP5 element operator, no Q, Q^T or mask; ceedbp_bk_apply) at N in {1, 2, 3, 5, 7,
-    9, 11, 15}, FP64 and FP32 pairs, on E = 2^k boxes with n = E N^3 from ~1e3 to ~1e8 (k in steps of 2):
+    9, 11, 15}, FP64 and FP32 pairs, on E = 2^k boxes (k <= 21) with n = E N^3 from ~1e3 to ~1e8 (k in steps of 2):
     time per apply (CUDA events over `--sweep-iters` applies after 3 warm-ups), algorithmic GFLOP/s
     (12 p1^4 + 15 p1^3 per element), DOFs/s and r_max, n_0.8 per (arith, N)."""
     import numpy as np
@@ -648,7 +648,7 @@ def run_bk_sweep(args):
             k = 0
             while 2 ** k * N ** 3 < 1e3:
                 k += 1
-            while 2 ** k * N ** 3 <= 1.2e8:
+            while 2 ** k * N ** 3 <= 1.2e8 and k <= 21:
                 dims = box_dims(k)
                 E = dims[0] * dims[1] * dims[2]
                 coords, l2g, dirichlet = pkg.mesh_box(*dims, N, 0.05)

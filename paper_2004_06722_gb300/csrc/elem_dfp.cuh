@@ -6,15 +6,15 @@
 // fetches the next element's data while it computes the current one, so the
 // dependent l2g -> u gather no longer stalls the warps:
 //
+//   top of element i:  plain loads of l2g of element i+1 (used an element phase later)
 //   end of the gradient phase of element i:
-//       cp.async  u of element i+1 (addresses from l2g of i+1, already in
-//                 shared memory), l2g of element i+2
+//       cp.async  u of element i+1 (addresses from those l2g registers)
 //   all along:  cp.async  G two slabs ahead, continuing into element i+1
 //   top of element i+1: wait for this thread's copies; convert u to pairs in
 //                 place; one barrier; compute
 //
-// Every thread copies and converts only its own column (i, j, 0..p1-1) of u,
-// l2g and G, so the only barriers are the three the contraction needs (after
+// Every thread copies and converts only its own column (i, j, 0..p1-1) of u
+// and G, so the only barriers are the three the contraction needs (after
 // the gather, after the gradient, and the element loop's top).  The u tile in
 // shared memory doubles as the pair tile of the r and s derivatives (rows of
 // p1+1 pairs, no bank conflicts between row and column reads).
@@ -24,8 +24,9 @@
 // through a private shared tile, and the fused (u, w) takes x_k from the front
 // of the column registers, shifted down once per slab.
 //
-// Shared memory per slot: 3-slab G ring, u tile, three gradient tiles, two
-// l2g buffers; for p1 = 8 and one component 31.7 KB.
+// Shared memory per slot: 3-slab G ring, u tile, r and s gradient tiles (rows
+// padded to p1+1 pairs), the private t tile; for p1 = 8 and one component
+// 26.5 KB, so four two-slot blocks fit on an SM.
 #pragma once
 
 #include "elem_df.cuh"
@@ -40,7 +41,7 @@ struct ElemDfpShape {
 };
 
 // layout: [red 32 NC doubles][smax 2 x 4 x 32 u32][sD p1 x (p1+1) pairs] then per slot:
-//         [G ring][sU NC tiles][sR NC tiles][sS NC tiles][sT NC tiles][sL 2 x p1^3 ints]
+//         [G ring][sU NC tiles][sR NC tiles][sS NC tiles][sT NC x p1^3 pairs]
 template <int P1, int NC>
 __host__ __device__ inline size_t elem_dfp_head_bytes() {
   const size_t h = sizeof(double) * 32 * NC + sizeof(unsigned) * 256 + sizeof(dfloat) * P1 * (P1 + 1);
@@ -50,7 +51,7 @@ __host__ __device__ inline size_t elem_dfp_head_bytes() {
 template <int P1, int NC>
 __host__ __device__ inline size_t elem_dfp_slot_bytes() {
   using S = ElemDfpShape<P1, NC>;
-  const size_t b = sizeof(dfloat) * (size_t(S::RING) + 4 * NC * size_t(S::TILE)) + sizeof(int) * 2 * S::P3;
+  const size_t b = sizeof(dfloat) * (size_t(S::RING) + 3 * NC * size_t(S::TILE) + size_t(NC) * S::P3);
   return (b + 15) / 16 * 16;
 }
 
@@ -85,8 +86,7 @@ __global__ void __launch_bounds__(P1 <= 8 ? 256 : 1024, (P1 <= 8 && NC == 1) ? 2
   dfloat* sU = ring + S::RING;
   dfloat* sR = sU + NC * TILE;
   dfloat* sS = sR + NC * TILE;
-  dfloat* sT = sS + NC * TILE;                        // private columns of the t components
-  int* sL = reinterpret_cast<int*>(sT + NC * TILE);  // [2][P3], private column entries
+  dfloat* sT = sS + NC * TILE;  // [NC][P3] private columns of the t components (unpadded)
   const int my = j * ROW + i;
 
   for (int q = tid; q < PP; q += blockDim.x) sD[(q / P1) * ROW + (q % P1)] = a.D[q];
@@ -98,17 +98,23 @@ __global__ void __launch_bounds__(P1 <= 8 ? 256 : 1024, (P1 <= 8 && NC == 1) ? 2
   auto elem_of = [&](int s) -> int64_t { return first + int64_t(s) * eb + slot; };
   auto live = [&](int s) -> bool { return in_slot && s < ns && elem_of(s) < m.nelem; };
 
-  // copy this thread's column of l2g of sequence entry s into buffer b
-  auto fetch_l2g = [&](int s, int b) {
+  // this thread's column of l2g of sequence entry s (plain loads, consumed an element later)
+  auto load_l2g = [&](int s, int (&lg)[P1]) {
     const int* src = m.l2g + elem_of(s) * P3 + t;
 #pragma unroll
-    for (int k = 0; k < P1; ++k) cp_async4(sL + b * P3 + k * PP + t, src + k * PP);
+    for (int k = 0; k < P1; ++k) lg[k] = __ldg(src + k * PP);
   };
-  // copy this thread's column of u (8 bytes per value: a double or a pair) using l2g in buffer b
-  auto fetch_u = [&](int b) {
+  auto dir_mask = [&](const int (&lg)[P1]) -> unsigned {
+    unsigned dm = 0u;
+#pragma unroll
+    for (int k = 0; k < P1; ++k) dm |= unsigned(lg[k] < 0) << k;
+    return dm;
+  };
+  // copy this thread's column of u (8 bytes per value: a double or a pair) to the u tile
+  auto fetch_u = [&](const int (&lg)[P1]) {
 #pragma unroll
     for (int k = 0; k < P1; ++k) {
-      const int g = sL[b * P3 + k * PP + t];
+      const int g = lg[k];
       const int64_t gg = g < 0 ? -int64_t(g) - 1 : int64_t(g);
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
@@ -125,13 +131,13 @@ __global__ void __launch_bounds__(P1 <= 8 ? 256 : 1024, (P1 <= 8 && NC == 1) ? 2
     for (int q = 0; q < 6; ++q) cp_async8(ring + rp * 6 * PP + q * PP + t, src + q * P3);
   };
 
-  // ---- prologue: l2g of entry 0, then u of entry 0, l2g of entry 1 and the first two G slabs
+  // ---- prologue: l2g and u of entry 0 and its first two G slabs
+  unsigned dmask = 0u;  // bit k: node (i, j, k) of the current entry is a Dirichlet node
   if (live(0)) {
-    fetch_l2g(0, 0);
-    cp_async_commit();
-    cp_async_wait_all();
-    fetch_u(0);
-    if (live(1)) fetch_l2g(1, 1);
+    int lg[P1];
+    load_l2g(0, lg);
+    dmask = dir_mask(lg);
+    fetch_u(lg);
     fetch_g(0, 0, 0);
     if (P1 > 1) fetch_g(0, 1, 1);
   }
@@ -148,16 +154,18 @@ __global__ void __launch_bounds__(P1 <= 8 ? 256 : 1024, (P1 <= 8 && NC == 1) ? 2
     unsigned* mx_s = smax + b * 128;        // [4][32] maxima of this entry
     unsigned* mx_o = smax + (b ^ 1) * 128;  // the other entry's, reset during this one
     cp_async_wait_all();
+    // l2g of the next entry: its loads fly during this entry's gather and gradient
+    int lg_next[P1];
+    const bool next_live = live(s + 1);
+    if (next_live) load_l2g(s + 1, lg_next);
 
     // ---- gather: own column of u to pairs (in place) and to registers
     dfloat xc[NC][P1];
-    unsigned dmask = 0u;
     float mx = 0.0f;
     if (active) {
 #pragma unroll
       for (int k = 0; k < P1; ++k) {
-        const bool dir = sL[b * P3 + k * PP + t] < 0;
-        dmask |= unsigned(dir) << k;
+        const bool dir = (dmask >> k) & 1u;
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
           dfloat* cell = sU + c * TILE + k * SLAB + my;
@@ -191,7 +199,6 @@ __global__ void __launch_bounds__(P1 <= 8 ? 256 : 1024, (P1 <= 8 && NC == 1) ? 2
         Di[n] = sD[i * ROW + n];
         Dj[n] = sD[j * ROW + n];
       }
-      const bool next_live = live(s + 1);
 #pragma unroll 1
       for (int k = 0; k < P1; ++k) {
         // prefetch the slab two ahead: this element's, or the next element's first two
@@ -241,7 +248,7 @@ __global__ void __launch_bounds__(P1 <= 8 ? 256 : 1024, (P1 <= 8 && NC == 1) ? 2
           const dfloat vr = wr.result(sg), vs = ws.result(sg), vt = wq.result(sg);
           sR[c * TILE + k * SLAB + my] = vr;
           sS[c * TILE + k * SLAB + my] = vs;
-          sT[c * TILE + k * SLAB + my] = vt;
+          sT[c * P3 + k * PP + t] = vt;
           mr = fmaxf(mr, fabsf(vr.hi));
           ms = fmaxf(ms, fabsf(vs.hi));
           mt = fmaxf(mt, fabsf(vt.hi));
@@ -253,9 +260,10 @@ __global__ void __launch_bounds__(P1 <= 8 ? 256 : 1024, (P1 <= 8 && NC == 1) ? 2
     slot_max<PP>(&mx_s[96 + slot], mt, active);
     __syncthreads();
     // every thread of the block is past its reads of this entry's u tile: fetch the next one
-    if (live(s + 1)) {
-      fetch_u(b ^ 1);
-      if (live(s + 2)) fetch_l2g(s + 2, b);
+    unsigned dmask_next = 0u;
+    if (next_live) {
+      fetch_u(lg_next);
+      dmask_next = dir_mask(lg_next);
     }
     cp_async_commit();
     const float sig_r = splitter(a.dnorm_col * __uint_as_float(mx_s[32 + slot]));
@@ -285,12 +293,12 @@ __global__ void __launch_bounds__(P1 <= 8 ? 256 : 1024, (P1 <= 8 && NC == 1) ? 2
           SplitAcc acr(sig_r), acs(sig_s), act(sig_t);
           const dfloat* rs = sR + c * TILE + k * SLAB;
           const dfloat* ss = sS + c * TILE + k * SLAB;
-          const dfloat* ts = sT + c * TILE + my;
+          const dfloat* ts = sT + c * P3 + t;
 #pragma unroll
           for (int n = 0; n < P1; ++n) {
             const dfloat vr = rs[j * ROW + n];
             const dfloat vs = ss[n * ROW + i];
-            const dfloat vt = ts[n * SLAB];
+            const dfloat vt = ts[n * PP];
             const dfloat dk = dkcol[n * P1];
             acr.add(Dni[n].hi, Dni[n].lo, vr.hi, vr.lo);
             acs.add(Dnj[n].hi, Dnj[n].lo, vs.hi, vs.lo);
@@ -310,6 +318,7 @@ __global__ void __launch_bounds__(P1 <= 8 ? 256 : 1024, (P1 <= 8 && NC == 1) ? 2
 #pragma unroll
       for (int c = 0; c < NC; ++c) dot[c] += df_to_f64(acc_dot[c]);
     }
+    dmask = dmask_next;
     // the next entry's gather rewrites the u tile only after its own copies land, and the
     // gradient tiles only after its first barrier, by which time every thread is done here
   }
