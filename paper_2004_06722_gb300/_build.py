@@ -27,8 +27,8 @@ def nvcc() -> str:
 def _compile(src: str, verbose: bool) -> str:
     obj = os.path.join(BUILD, os.path.basename(src) + ".o")
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(
-            os.path.getmtime(p) for p in [src] + glob.glob(os.path.join(CSRC, "*.h*")) +
-            glob.glob(os.path.join(ROOT, "include", "*.h"))):
+            os.path.getmtime(p) for p in [src] + glob.glob(os.path.join(CSRC, "*.h")) +
+            glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(ROOT, "include", "*.h"))):
         return obj
     extra = ["-Xptxas", "-v"] if verbose else []
     cmd = [nvcc()] + ARCH + FLAGS + extra + ["-c", src, "-o", obj]

@@ -22,10 +22,11 @@
 namespace ceedbp {
 
 // GLL derivative matrices as pairs, one slot of kMaxP1^2 per order (p1 - 2):
-// the t-direction operands D[k][n] have compile-time indices and are read
-// straight from the constant bank by the FMAs.  Defined here: this header is
-// included by the one translation unit that instantiates the kernels.
-__constant__ dfloat c_Ddf[kMaxP1 - 1][kMaxP1 * kMaxP1];
+// the t-direction operands D[k][n] are read straight from the constant bank.
+// Internal linkage: every translation unit that instantiates the kernels (one
+// per group of orders, compiled in parallel) has its own copy and its own
+// setter (elem_df_group.cuh).
+static __constant__ dfloat c_Ddf[kMaxP1 - 1][kMaxP1 * kMaxP1];
 
 template <int P1, int NC, bool STAGE>
 struct ElemDfShape {

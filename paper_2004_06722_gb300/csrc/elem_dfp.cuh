@@ -1,4 +1,5 @@
-// Software-pipelined variant of the FP32-pair BK5/BK6 element kernel.
+// Software-pipelined variant of the FP32-pair BK5/BK6 element kernel
+// (instantiated for p1 <= 16 with one component, p1 <= 8 with three).
 //
 // Same arithmetic as elem_df_kernel (splitter accumulation, per-direction
 // transpose accumulators, fused (u, w) and alpha), different schedule: each
@@ -65,8 +66,10 @@ __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// Register cap: for p1 <= 8 (one component) two 256-thread blocks per SM; above p1 = 8 one
+// slot per block (p1^2 threads), so a thread may use up to 255 registers.
 template <int P1, int NC>
-__global__ void __launch_bounds__(P1 <= 8 ? 256 : 1024, (P1 <= 8 && NC == 1) ? 2 : 1)
+__global__ void __launch_bounds__(P1 <= 8 ? 256 : ((P1 * P1 + 31) / 32) * 32, (P1 <= 8 && NC == 1) ? 2 : 1)
     elem_dfp_kernel(const DeviceMesh m, const ElemDfArgs a, const int eb, const int ns) {
   using S = ElemDfpShape<P1, NC>;
   constexpr int PP = S::PP, P3 = S::P3, ROW = S::ROW, SLAB = S::SLAB, TILE = S::TILE;

@@ -88,10 +88,16 @@ __global__ void pcg_update_kernel(const int* __restrict__ off, const int* __rest
     const int o0 = __ldg(off + g);
     if (o0 < 0) continue;  // Dirichlet node: x, r, p stay zero
     const int o1 = __ldg(off + g + 1) & 0x7fffffff;
+    // start from the first slot (one FP64 add fewer per node); a node no element touches sums to 0
     double w[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) w[c] = 0.0;
-    for (int k = o0; k < o1; ++k) {
+    if (o0 < o1) {
+      const int sl = __ldg(slots + o0);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) w[c] = __ldcs(wl + size_t(sl) * NC + c);
+    }
+    for (int k = o0 + 1; k < o1; ++k) {
       const int sl = __ldg(slots + k);
 #pragma unroll
       for (int c = 0; c < NC; ++c) w[c] += __ldcs(wl + size_t(sl) * NC + c);

@@ -90,10 +90,20 @@ __global__ void update_df_kernel(const int* __restrict__ off, const int* __restr
     const int o0 = __ldg(off + g);
     if (o0 < 0) continue;
     const int o1 = __ldg(off + g + 1) & 0x7fffffff;
+    // start from the first slot (the local values are normalised pairs, so this equals adding
+    // them to zero); a node no element touches sums to 0
     dfloat w[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) w[c] = dfloat{0.0f, 0.0f};
-    for (int k = o0; k < o1; ++k) {
+    if (o0 < o1) {
+      const int sl = __ldg(slots + o0);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const float2 v = __ldcs(reinterpret_cast<const float2*>(wl + size_t(sl) * NC + c));
+        w[c] = dfloat{v.x, v.y};
+      }
+    }
+    for (int k = o0 + 1; k < o1; ++k) {
       const int sl = __ldg(slots + k);
 #pragma unroll
       for (int c = 0; c < NC; ++c) {

@@ -119,7 +119,8 @@ PIPELINED = [(1, 4), (1, 8), (1, 16), (2, 4), (2, 16)]
 
 
 @pytest.mark.parametrize("bp,N,dims", [(5, 1, (3, 2, 2)), (5, 3, (3, 2, 5)), (5, 4, (2, 3, 3)), (5, 5, (3, 3, 2)),
-                                        (5, 7, (5, 3, 3)), (6, 3, (2, 3, 2)), (6, 7, (3, 2, 2))])
+                                        (5, 7, (5, 3, 3)), (6, 3, (2, 3, 2)), (6, 7, (3, 2, 2)), (5, 9, (3, 1, 2)),
+                                        (5, 11, (2, 1, 2)), (5, 15, (1, 1, 2))])
 def test_pipelined_schedule_parity_and_same_bits(bp, N, dims):
     """Every pair-kernel schedule computes the same element results: the pipelined
     sequences (ragged last block: E is not a multiple of eb * seq) match the oracle
