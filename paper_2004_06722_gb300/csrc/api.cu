@@ -326,7 +326,12 @@ ceedbp_status setup_impl(ceedbp_ctx* c, const double* coords, const int64_t* l2g
       m.tune_eb = cand_eb[k];
       m.tune_stage = cand_st[k];
       m.tune_ns = cand_ns[k];
-      CK(c, launch_elem_df(m, a, s));  // warm-up of this shape
+      {  // warm-up of this shape
+        const cudaError_t e = launch_elem_df(m, a, s);
+        if (e != cudaSuccess)
+          return cuda_fail(c, e, ("pair kernel shape eb=" + std::to_string(m.tune_eb) + " schedule=" +
+                                  std::to_string(m.tune_stage) + " seq=" + std::to_string(m.tune_ns)).c_str());
+      }
       CK(c, cudaEventRecord(c->ev0, s));
       for (int r = 0; r < 3; ++r) CK(c, launch_elem_df(m, a, s));
       CK(c, cudaEventRecord(c->ev1, s));

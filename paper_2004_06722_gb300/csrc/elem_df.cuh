@@ -393,6 +393,9 @@ inline bool elem_df_shape_ok(int eb) {
   const int nthreads = ((eb * P1 * P1 + 31) / 32) * 32;
   if (smem > kMaxSmemPerBlock || nthreads > 1024) return false;
   if (elem_df_attr<P1, NC, STAGE>() != cudaSuccess) return false;
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, elem_df_kernel<P1, NC, STAGE>) != cudaSuccess || nthreads > fa.maxThreadsPerBlock)
+    return false;
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, elem_df_kernel<P1, NC, STAGE>, nthreads, smem) !=
       cudaSuccess)

@@ -367,6 +367,10 @@ inline bool elem_dfp_shape_ok(int eb) {
   const int nthreads = ((eb * P1 * P1 + 31) / 32) * 32;
   if (smem > kMaxSmemPerBlock || nthreads > 1024) return false;
   if (elem_dfp_attr<P1, NC>() != cudaSuccess) return false;
+  // the launch bound caps the block size (the occupancy query alone does not reject larger blocks)
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, elem_dfp_kernel<P1, NC>) != cudaSuccess || nthreads > fa.maxThreadsPerBlock)
+    return false;
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, elem_dfp_kernel<P1, NC>, nthreads, smem) != cudaSuccess)
     return false;
