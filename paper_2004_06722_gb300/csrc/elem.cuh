@@ -45,8 +45,16 @@ inline size_t elem_smem_bytes(int eb) {
   return sizeof(double) * (size_t(Q) * P1 + size_t(Q) * Q + size_t(eb) * S::NBUF * NC * S::Q3 + 32 * NC);
 }
 
+// Threads of one block (whole warps); the launch bound below lets the compiler
+// size registers for exactly this block.
+template <int Q, int NC>
+constexpr int elem_threads() {
+  return (((256 / (Q * Q * NC) < 1 ? 1 : 256 / (Q * Q * NC)) * Q * Q + 31) / 32) * 32;
+}
+
 template <int P1, int Q, bool COLLOC, int KIND, int NC>
-__global__ void elem_kernel(const DeviceMesh m, const ElemArgs a, const int eb) {
+__global__ void __launch_bounds__(elem_threads<Q, NC>()) elem_kernel(const DeviceMesh m, const ElemArgs a,
+                                                                     const int eb) {
   using S = ElemShape<P1, Q, COLLOC>;
   constexpr int QQ = S::QQ, Q3 = S::Q3, P3 = S::P3;
   extern __shared__ double smem[];
