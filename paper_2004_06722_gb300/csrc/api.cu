@@ -888,6 +888,14 @@ ceedbp_status ceedbp_set_helmholtz(ceedbp_ctx* c, double beta) {
   helm_diag_kernel<<<1216, 256, 0, s>>>(c->d_r, c->d_ax, beta, c->d_r, n);
   CK(c, cudaGetLastError());
   CK(c, launch_dinv(c->d_off, c->d_r, c->d_dinv, n, s));
+  // one launch of the element kernel variant now in use, outside any graph capture
+  ElemArgs a{};
+  a.u = c->d_r;
+  a.wl = c->d_wl;
+  a.G = c->d_G;
+  a.mask_in = 1;
+  set_helmholtz_args(c, a);
+  CK(c, launch_elem(m, kStiff, a, s));
   CK(c, cudaStreamSynchronize(s));
   return CEEDBP_OK;
 }

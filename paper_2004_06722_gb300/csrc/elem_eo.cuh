@@ -47,7 +47,9 @@ __device__ __forceinline__ int eo_node(int i, int j, int k, int bi, int bj, int 
   return ii + P1 * (jj + P1 * kk);
 }
 
-template <int P1, int NC>
+// HELM: the Helmholtz term beta B u of Eq. (17) is compiled in only for beta != 0, so the plain
+// stiffness kernel carries no extra registers or branches.
+template <int P1, int NC, bool HELM>
 __global__ void elem_eo_kernel(const DeviceMesh m, const ElemArgs a, const int eb) {
   using S = EoShape<P1>;
   constexpr int H = S::H, H3 = S::H3, P3 = S::P3, HALF = S::HALF;
@@ -285,7 +287,7 @@ __global__ void elem_eo_kernel(const DeviceMesh m, const ElemArgs a, const int e
 #pragma unroll
       for (int c8 = 0; c8 < 8; ++c8) {
         const int node = eo_node<P1>(i, j, k, c8 & 1, (c8 >> 1) & 1, c8 >> 2);
-        if (a.beta != 0.0) w[c8] += a.beta * __ldg(a.Mq + e * P3 + node) * u[c][c8];  // Eq. (17)
+        if constexpr (HELM) w[c8] += a.beta * __ldg(a.Mq + e * P3 + node) * u[c][c8];  // Eq. (17)
         if (!(a.skip_dirichlet_out && ((dmask >> c8) & 1))) wl[size_t(node) * NC + c] = w[c8];
         dot[c] += w[c8] * u[c][c8];
       }
@@ -318,17 +320,22 @@ __global__ void elem_eo_kernel(const DeviceMesh m, const ElemArgs a, const int e
   }
 }
 
-template <int P1, int NC>
-cudaError_t launch_elem_eo_t(const DeviceMesh& m, const ElemArgs& a, cudaStream_t s) {
+template <int P1, int NC, bool HELM>
+cudaError_t launch_elem_eo_h(const DeviceMesh& m, const ElemArgs& a, cudaStream_t s) {
   const int eb = elem_eo_per_block<P1, NC>();
   const int nthreads = ((eb * EoShape<P1>::H3 + 31) / 32) * 32;
   const size_t smem = elem_eo_smem_bytes<P1, NC>(eb);
-  auto kern = elem_eo_kernel<P1, NC>;
+  auto kern = elem_eo_kernel<P1, NC, HELM>;
   static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (attr != cudaSuccess) return attr;
   const int64_t blocks = (m.nelem + eb - 1) / eb;
   kern<<<unsigned(blocks), nthreads, smem, s>>>(m, a, eb);
   return cudaGetLastError();
+}
+
+template <int P1, int NC>
+cudaError_t launch_elem_eo_t(const DeviceMesh& m, const ElemArgs& a, cudaStream_t s) {
+  return a.beta != 0.0 ? launch_elem_eo_h<P1, NC, true>(m, a, s) : launch_elem_eo_h<P1, NC, false>(m, a, s);
 }
 
 // whether the kernel can be resident (its registers and threads fit an SM)
@@ -338,13 +345,18 @@ inline bool elem_eo_launchable() {
     const int eb = elem_eo_per_block<P1, NC>();
     const int nthreads = ((eb * EoShape<P1>::H3 + 31) / 32) * 32;
     const size_t smem = elem_eo_smem_bytes<P1, NC>(eb);
-    if (cudaFuncSetAttribute(elem_eo_kernel<P1, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) !=
-        cudaSuccess)
+    int nb0 = 0, nb1 = 0;
+    if (cudaFuncSetAttribute(elem_eo_kernel<P1, NC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(smem)) != cudaSuccess ||
+        cudaFuncSetAttribute(elem_eo_kernel<P1, NC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(smem)) != cudaSuccess)
       return false;
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, elem_eo_kernel<P1, NC>, nthreads, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb0, elem_eo_kernel<P1, NC, false>, nthreads, smem) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb1, elem_eo_kernel<P1, NC, true>, nthreads, smem) !=
+            cudaSuccess)
       return false;
-    return nb >= 1;
+    return nb0 >= 1 && nb1 >= 1;
   }();
   return ok;
 }
