@@ -16,7 +16,13 @@
  * assembled operator applied matrix-free as w = Q^T A_L Q u (Eq. (21)), the
  * element operators in the factored form of Eq. (22) (stiffness) or Eq. (34)
  * (mass) with geometric factors G^e_mm' of Eq. (23), and diagonally
- * preconditioned CG around them (Sec. 3).
+ * preconditioned CG around them (Sec. 3).  Around that path: the Helmholtz
+ * operator A + beta B of Eq. (17) (ceedbp_set_helmholtz), a variable
+ * coefficient with its adjoint gradient (ceedbp_set_kappa,
+ * ceedbp_kappa_gradient), FP64 defect correction around FP32/BF16 inner
+ * solves (ceedbp_prepare_mixed), batched solves (ceedbp_batch_*), the
+ * unassembled element operators (ceedbp_bk_apply) and an allocation-free
+ * apply (ceedbp_apply_noalloc).
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -61,7 +67,8 @@ enum {
   CEEDBP_ARITH_FP64 = 0, /* native FP64 instructions */
   CEEDBP_ARITH_DF64 = 1  /* FP64-accurate pairs of FP32 numbers (hi + lo, ~2^-46 relative per
                             value) on the FP32 pipe, which the GB300 issues 59x faster than
-                            FP64; BP5 and BP6 only.  Results match the FP64 path to ~1e-14. */
+                            FP64; BP5 and BP6 only.  One apply matches the FP64 path to about
+                            2e-13 relative and the FP64 oracle to below 1e-12. */
 };
 
 typedef struct {
