@@ -61,11 +61,6 @@ inline size_t elem_dfp_smem_bytes(int eb) {
   return elem_dfp_head_bytes<P1, NC>() + size_t(eb) * elem_dfp_slot_bytes<P1, NC>();
 }
 
-__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
 // Register cap: for p1 <= 8 (one component) two 256-thread blocks per SM; above p1 = 8 one
 // slot per block (p1^2 threads), so a thread may use up to 255 registers.
 template <int P1, int NC>

@@ -1,14 +1,15 @@
 // Low-precision element kernel instantiations (orders 1..15; FP32 or BF16
-// storage; one or three components), see elem_lp.cuh.
-#include "elem_lp.cuh"
+// storage; one or three components), see elem_lp.cuh; FP32 storage runs the
+// pipelined schedule of elem_lpp.cuh where its shape fits.
+#include "elem_lpp.cuh"
 
 namespace ceedbp {
 
 template <int P1>
 static cudaError_t launch_lp_p(const DeviceMesh& m, const ElemLpArgs& a, int bf16, cudaStream_t s) {
   if (m.ncomp == 3)
-    return bf16 ? launch_elem_lp_t<P1, 3, __nv_bfloat16>(m, a, s) : launch_elem_lp_t<P1, 3, float>(m, a, s);
-  return bf16 ? launch_elem_lp_t<P1, 1, __nv_bfloat16>(m, a, s) : launch_elem_lp_t<P1, 1, float>(m, a, s);
+    return bf16 ? launch_elem_lp_t<P1, 3, __nv_bfloat16>(m, a, s) : launch_elem_lpp_t<P1, 3>(m, a, s);
+  return bf16 ? launch_elem_lp_t<P1, 1, __nv_bfloat16>(m, a, s) : launch_elem_lpp_t<P1, 1>(m, a, s);
 }
 
 #define CEEDBP_LP_CASE(P) \
