@@ -133,13 +133,20 @@ __global__ void inner_update_kernel(const int* __restrict__ off, const int* __re
     const int o0 = __ldg(off + g);
     if (o0 < 0) continue;
     const int o1 = __ldg(off + g + 1) & 0x7fffffff;
+    // two slots per step (their loads are independent); a node no element touches sums to 0
     float w[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) w[c] = 0.0f;
-    for (int k = o0; k < o1; ++k) {
-      const int sl = __ldg(slots + k);
+    int k = o0;
+    for (; k + 1 < o1; k += 2) {
+      const int s0 = __ldg(slots + k), s1 = __ldg(slots + k + 1);
 #pragma unroll
-      for (int c = 0; c < NC; ++c) w[c] += __ldcs(wl + size_t(sl) * NC + c);
+      for (int c = 0; c < NC; ++c) w[c] += __ldcs(wl + size_t(s0) * NC + c) + __ldcs(wl + size_t(s1) * NC + c);
+    }
+    if (k < o1) {
+      const int s0 = __ldg(slots + k);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) w[c] += __ldcs(wl + size_t(s0) * NC + c);
     }
     const float di = dinv[g];
 #pragma unroll
