@@ -97,10 +97,21 @@ __global__ void pcg_update_kernel(const int* __restrict__ off, const int* __rest
 #pragma unroll
       for (int c = 0; c < NC; ++c) w[c] = __ldcs(wl + size_t(sl) * NC + c);
     }
-    for (int k = o0 + 1; k < o1; ++k) {
-      const int sl = __ldg(slots + k);
+    // the remaining slots two at a time (loads issued together, sums in slot order)
+    int k = o0 + 1;
+    for (; k + 1 < o1; k += 2) {
+      const int s0 = __ldg(slots + k), s1 = __ldg(slots + k + 1);
 #pragma unroll
-      for (int c = 0; c < NC; ++c) w[c] += __ldcs(wl + size_t(sl) * NC + c);
+      for (int c = 0; c < NC; ++c) {
+        const double v0 = __ldcs(wl + size_t(s0) * NC + c), v1 = __ldcs(wl + size_t(s1) * NC + c);
+        w[c] += v0;
+        w[c] += v1;
+      }
+    }
+    if (k < o1) {
+      const int s0 = __ldg(slots + k);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) w[c] += __ldcs(wl + size_t(s0) * NC + c);
     }
     const double di = dinv[g];
 #pragma unroll

@@ -103,11 +103,23 @@ __global__ void update_df_kernel(const int* __restrict__ off, const int* __restr
         w[c] = dfloat{v.x, v.y};
       }
     }
-    for (int k = o0 + 1; k < o1; ++k) {
-      const int sl = __ldg(slots + k);
+    // the remaining slots two at a time (loads issued together, sums in slot order)
+    int k = o0 + 1;
+    for (; k + 1 < o1; k += 2) {
+      const int s0 = __ldg(slots + k), s1 = __ldg(slots + k + 1);
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
-        const float2 v = __ldcs(reinterpret_cast<const float2*>(wl + size_t(sl) * NC + c));
+        const float2 v0 = __ldcs(reinterpret_cast<const float2*>(wl + size_t(s0) * NC + c));
+        const float2 v1 = __ldcs(reinterpret_cast<const float2*>(wl + size_t(s1) * NC + c));
+        w[c] = dw_add(w[c], dfloat{v0.x, v0.y});
+        w[c] = dw_add(w[c], dfloat{v1.x, v1.y});
+      }
+    }
+    if (k < o1) {
+      const int s0 = __ldg(slots + k);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const float2 v = __ldcs(reinterpret_cast<const float2*>(wl + size_t(s0) * NC + c));
         w[c] = dw_add(w[c], dfloat{v.x, v.y});
       }
     }
