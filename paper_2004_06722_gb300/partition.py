@@ -15,9 +15,9 @@ This module holds the partition-ready data structures for that split:
   into the global sum on its interface nodes through ``torch.distributed``
   (one all-reduce over the union of interface nodes, in a fixed order).
 
-Every box of this build has one GPU, so solves run as independent replicas and
-this exchange is exercised on CPU ranks (gloo); it is the stage a multi-GPU
-solve would insert between the element kernel and the vector update.
+Solves on the GPU run as independent replicas (one per rank), so this exchange is
+exercised on CPU ranks (gloo); it is the stage a multi-GPU solve would insert
+between the element kernel and the vector update.
 """
 from __future__ import annotations
 

@@ -1,7 +1,7 @@
 """Multi-rank host logic on CPU (gloo, world size 2): the interface exchange of a
 distributed Q^T reproduces the assembled operator, the per-element dot of
 Algorithm 1 sums to p^T A p across ranks, and the bench's whole-job time is the
-maximum over ranks.  (Every GPU machine has one GPU: solves run as replicas.)"""
+maximum over ranks.  On the GPU the solves run as independent replicas, one per rank."""
 import os
 import socket
 
