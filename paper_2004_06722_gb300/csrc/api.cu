@@ -318,7 +318,7 @@ ceedbp_status setup_impl(ceedbp_ctx* c, const double* coords, const int64_t* l2g
     CK(c, cudaStreamSynchronize(s));
     // autotuner: elements per block and G staging of the pair kernel, timed on this mesh
     int cand_eb[32], cand_st[32], cand_ns[32];
-    const int ncand = elem_df_tile_candidates(m, cand_eb, cand_st, cand_ns, 32, !c->no_pipeline);
+    const int ncand = elem_df_tile_candidates(m, cand_eb, cand_st, cand_ns, 32, true);
     if (ncand == 0) return fail(c, CEEDBP_EUNSUPPORTED, "no launchable shape for the pair kernel at this order");
     float best = 1e30f;
     int best_k = 0;
@@ -936,7 +936,7 @@ ceedbp_status ceedbp_set_tile(ceedbp_ctx* c, int eb, int schedule, int seq) {
   if (!c) return fail(c, CEEDBP_EINVAL, "null context");
   if (c->arith != CEEDBP_ARITH_DF64) return fail(c, CEEDBP_EUNSUPPORTED, "tile shapes belong to the pair path");
   int cand_eb[32], cand_st[32], cand_ns[32];
-  const int ncand = elem_df_tile_candidates(c->mesh, cand_eb, cand_st, cand_ns, 32, !c->no_pipeline);
+  const int ncand = elem_df_tile_candidates(c->mesh, cand_eb, cand_st, cand_ns, 32, true);
   int hit = -1;
   for (int k = 0; k < ncand; ++k)
     if (cand_eb[k] == eb && cand_st[k] == schedule && (schedule != 2 || cand_ns[k] == seq)) hit = k;

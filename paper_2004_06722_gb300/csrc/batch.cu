@@ -317,15 +317,15 @@ ceedbp_status ceedbp_batch_setup(int nprob, const ceedbp_params* params, const d
     if (!g.ctx) return fail_out(bfail(nullptr, CEEDBP_ENOMEM, "host allocation failed"));
     g.ctx->prm = ceedbp_params{5, N, 0, E, ng, CEEDBP_ARITH_DF64};
     g.ctx->stream = b->stream;
-    g.ctx->no_pipeline = true;
     ceedbp_status st = setup_context(g.ctx, cc.data(), ll.data(), dd.data(), nullptr);
     if (st != CEEDBP_OK) {
       const std::string msg = g.ctx->err;
       b->groups.push_back(g);
       return fail_out(bfail(nullptr, st, "group setup: " + msg));
     }
-    // block tables with the autotuned elements per block of this order
-    const int eb = std::max(1, g.ctx->mesh.tune_eb);
+    // block tables with the autotuned shape of this order: elements per block, times the
+    // sequence length of the pipelined schedule
+    const int eb = std::max(1, g.ctx->mesh.tune_eb) * (g.ctx->mesh.tune_stage == 2 ? g.ctx->mesh.tune_ns : 1);
     std::vector<int> bp, be0, bn, pb0, pnb, vp, vn0, vn1, vb0, vnb, n0;
     eo = 0;
     for (size_t k = 0; k < g.members.size(); ++k) {

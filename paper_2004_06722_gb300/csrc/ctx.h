@@ -40,7 +40,6 @@ struct ceedbp_ctx {
   // scratch d_wl (a pair has the size of a double).
   int arith = 0;
   double beta = 0.0;  // Helmholtz coefficient of Eq. (17) (ceedbp_set_helmholtz)
-  bool no_pipeline = false;  // batched groups: the pipelined pair schedule has no per-problem block tables
   ceedbp::dfloat* d_Gdf = nullptr;
   ceedbp::dfloat* d_Ddf = nullptr;
   ceedbp::dfloat* d_dinvdf = nullptr;

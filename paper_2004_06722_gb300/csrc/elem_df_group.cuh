@@ -20,7 +20,7 @@ constexpr bool kDfpBuilt = (NC == 1) || (P1 <= 8);
 template <int P1, int NC>
 cudaError_t launch_df_any(const DeviceMesh& m, const ElemDfArgs& a, cudaStream_t s) {
   if constexpr (kDfpBuilt<P1, NC>) {
-    if (m.tune_stage == 2 && a.blk_prob == nullptr) return launch_elem_dfp_t<P1, NC>(m, a, s);
+    if (m.tune_stage == 2) return launch_elem_dfp_t<P1, NC>(m, a, s);
   }
   return launch_elem_df_t<P1, NC>(m, a, s);
 }

@@ -91,10 +91,21 @@ __global__ void __launch_bounds__(P1 <= 8 ? 256 : ((P1 * P1 + 31) / 32) * 32, (P
   for (int q = tid; q < 256; q += blockDim.x) smax[q] = 0u;
   __syncthreads();
 
-  // elements of this slot: e(s) = first + s * eb + slot, s = 0 .. ns-1
-  const int64_t first = int64_t(blockIdx.x) * eb * ns;
+  // elements of this slot: e(s) = first + s * eb + slot, s = 0 .. ns-1, the first `count`
+  // elements from `first` (batched solves: one problem's range per block, from the block tables)
+  int64_t first = int64_t(blockIdx.x) * eb * ns;
+  int64_t count = int64_t(eb) * ns;
+  int prob = 0;
+  if (a.blk_prob != nullptr) {
+    prob = a.blk_prob[blockIdx.x];
+    if (!a.bst[prob].c.active) return;  // the whole block belongs to one problem
+    first = a.blk_e0[blockIdx.x];
+    count = a.blk_n[blockIdx.x];
+  }
   auto elem_of = [&](int s) -> int64_t { return first + int64_t(s) * eb + slot; };
-  auto live = [&](int s) -> bool { return in_slot && s < ns && elem_of(s) < m.nelem; };
+  auto live = [&](int s) -> bool {
+    return in_slot && s < ns && int64_t(s) * eb + slot < count && elem_of(s) < m.nelem;
+  };
 
   // this thread's column of l2g of sequence entry s (plain loads, consumed an element later)
   auto load_l2g = [&](int s, int (&lg)[P1]) {
@@ -322,6 +333,26 @@ __global__ void __launch_bounds__(P1 <= 8 ? 256 : ((P1 * P1 + 31) / 32) * 32, (P
   }
   cp_async_wait_all();
 
+  if constexpr (NC == 1) {
+    if (a.blk_prob != nullptr) {  // per-problem alpha from a segmented last-block reduction
+      const int b0 = a.prob_blk0[prob];
+      if (grid_sum_last<1>(dot, a.partials + b0, a.prob_nblk[prob], int(blockIdx.x) - b0,
+                           &a.bst[prob].ticket[kTicketApply], red)) {
+        if (threadIdx.x == 0) {
+          CompScalars& cs = a.bst[prob].c;
+          const double pAp = dot[0];
+          cs.pAp = pAp;
+          if (!(pAp > 0.0) || !isfinite(pAp) || !isfinite(cs.rz)) {
+            cs.status = CEEDBP_EBREAKDOWN;
+            cs.alpha = 0.0;
+          } else {
+            cs.alpha = cs.rz / pAp;
+          }
+        }
+      }
+      return;
+    }
+  }
   if (a.partials != nullptr) {
     if (grid_sum_last<NC>(dot, a.partials, gridDim.x, blockIdx.x, &a.state->ticket[kTicketApply], red)) {
       if (threadIdx.x == 0) {
@@ -382,7 +413,7 @@ cudaError_t launch_elem_dfp_t(const DeviceMesh& m, const ElemDfArgs& a, cudaStre
   const cudaError_t attr = elem_dfp_attr<P1, NC>();
   if (attr != cudaSuccess) return attr;
   const int64_t per_block = int64_t(eb) * ns;
-  const int64_t blocks = (m.nelem + per_block - 1) / per_block;
+  const int64_t blocks = a.blk_prob != nullptr ? int64_t(a.batch_blocks) : (m.nelem + per_block - 1) / per_block;
   elem_dfp_kernel<P1, NC><<<unsigned(blocks), nthreads, smem, s>>>(m, a, eb, ns);
   return cudaGetLastError();
 }
