@@ -318,7 +318,17 @@ ceedbp_status setup_impl(ceedbp_ctx* c, const double* coords, const int64_t* l2g
     CK(c, cudaStreamSynchronize(s));
     // autotuner: elements per block and G staging of the pair kernel, timed on this mesh
     int cand_eb[32], cand_st[32], cand_ns[32];
-    const int ncand = elem_df_tile_candidates(m, cand_eb, cand_st, cand_ns, 32, true);
+    int ncand = elem_df_tile_candidates(m, cand_eb, cand_st, cand_ns, 32, true);
+    if (c->pipelined_only) {  // keep the pipelined shapes when there are any
+      int np = 0;
+      for (int k = 0; k < ncand; ++k)
+        if (cand_st[k] == 2) {
+          cand_eb[np] = cand_eb[k];
+          cand_st[np] = cand_st[k];
+          cand_ns[np++] = cand_ns[k];
+        }
+      if (np > 0) ncand = np;
+    }
     if (ncand == 0) return fail(c, CEEDBP_EUNSUPPORTED, "no launchable shape for the pair kernel at this order");
     float best = 1e30f;
     int best_k = 0;

@@ -317,6 +317,7 @@ ceedbp_status ceedbp_batch_setup(int nprob, const ceedbp_params* params, const d
     if (!g.ctx) return fail_out(bfail(nullptr, CEEDBP_ENOMEM, "host allocation failed"));
     g.ctx->prm = ceedbp_params{5, N, 0, E, ng, CEEDBP_ARITH_DF64};
     g.ctx->stream = b->stream;
+    g.ctx->pipelined_only = true;  // large concatenated meshes: the pipelined schedule wins
     ceedbp_status st = setup_context(g.ctx, cc.data(), ll.data(), dd.data(), nullptr);
     if (st != CEEDBP_OK) {
       const std::string msg = g.ctx->err;

@@ -39,6 +39,7 @@ struct ceedbp_ctx {
   // Jacobi inverse; the CG pair vectors reuse d_r, d_p, d_ax and the local
   // scratch d_wl (a pair has the size of a double).
   int arith = 0;
+  bool pipelined_only = false;  // batched groups: tune among the pipelined pair-kernel shapes only
   double beta = 0.0;  // Helmholtz coefficient of Eq. (17) (ceedbp_set_helmholtz)
   ceedbp::dfloat* d_Gdf = nullptr;
   ceedbp::dfloat* d_Ddf = nullptr;
