@@ -15,8 +15,8 @@
 //                 place; one barrier; compute
 //
 // Every thread copies and converts only its own column (i, j, 0..p1-1) of u
-// and G, so the only barriers are the three the contraction needs (after
-// the gather, after the gradient, and the element loop's top).  The u tile in
+// and G, so each element needs only the two barriers of the contraction (after
+// the gather and after the gradient phase).  The u tile in
 // shared memory doubles as the pair tile of the r and s derivatives (rows of
 // p1+1 pairs, no bank conflicts between row and column reads).
 //
@@ -27,7 +27,9 @@
 //
 // Shared memory per slot: 3-slab G ring, u tile, r and s gradient tiles (rows
 // padded to p1+1 pairs), the private t tile; for p1 = 8 and one component
-// 26.5 KB, so four two-slot blocks fit on an SM.
+// 26.5 KB, so four two-slot blocks fit on an SM.  Batched solves pass block
+// tables (one problem's range of elements per block) and get a per-problem
+// alpha from a segmented reduction, as in elem_df_kernel.
 #pragma once
 
 #include "elem_df.cuh"
