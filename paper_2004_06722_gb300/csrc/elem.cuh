@@ -32,6 +32,79 @@ struct ElemShape {
   static constexpr int NBUF = COLLOC ? 3 : 4;
 };
 
+// Even-odd form (Eq. (37)) of a product y = M x with M centro-symmetric
+// (SIGN = +1: M[A-1-a][B-1-b] = M[a][b], the interpolation J and J^T) or
+// centro-antisymmetric (SIGN = -1: the derivative D and D^T).  With
+// x+_b = x_b + x_{B-1-b}, x-_b = x_b - x_{B-1-b} (b < B/2) and the half tables
+// E = (M[a][b] + M[a][B-1-b]) / 2, O = (M[a][b] - M[a][B-1-b]) / 2 of the top
+// rows (a < (A+1)/2), plus the middle column M[a][B/2] when B is odd:
+//   y_a = S_E + S_O,  y_{A-1-a} = SIGN (S_E - S_O),
+// and for odd A the middle row is S_E (SIGN = +1) or S_O (SIGN = -1).  About
+// half the multiply-adds of the direct product; used for the contractions
+// that stay in a thread's registers.
+template <int A, int B>
+struct EoTab {
+  static constexpr int HA = (A + 1) / 2, HB = B / 2;
+  static constexpr int SIZE = 2 * HA * HB + HA;  // [E HA x HB][O HA x HB][middle column HA]
+};
+
+// tables of row-major M (A x B, leading dimension ld, element (a, b) at M[a * ld + b],
+// or M[b * ld + a] when TRANS) into T
+template <int A, int B, bool TRANS>
+__device__ __forceinline__ void eo_build(const double* M, int ld, double* T, int tid, int nthr) {
+  using E = EoTab<A, B>;
+  for (int q = tid; q < E::HA * E::HB; q += nthr) {
+    const int ra = q / E::HB, cb = q % E::HB;
+    const double m0 = TRANS ? M[cb * ld + ra] : M[ra * ld + cb];
+    const double m1 = TRANS ? M[(B - 1 - cb) * ld + ra] : M[ra * ld + B - 1 - cb];
+    T[q] = 0.5 * (m0 + m1);
+    T[E::HA * E::HB + q] = 0.5 * (m0 - m1);
+  }
+  if constexpr (B % 2 == 1)
+    for (int ra = tid; ra < E::HA; ra += nthr) T[2 * E::HA * E::HB + ra] = TRANS ? M[(B / 2) * ld + ra] : M[ra * ld + B / 2];
+}
+
+template <int A, int B, int SIGN>
+__device__ __forceinline__ void eo_mul(const double* T, const double (&x)[B], double (&y)[A]) {
+  using E = EoTab<A, B>;
+  constexpr int HA = E::HA, HB = E::HB;
+  const double* TE = T;
+  const double* TO = T + HA * HB;
+  const double* TM = T + 2 * HA * HB;
+  double xe[HB > 0 ? HB : 1], xo[HB > 0 ? HB : 1];
+#pragma unroll
+  for (int b = 0; b < HB; ++b) {
+    xe[b] = x[b] + x[B - 1 - b];
+    xo[b] = x[b] - x[B - 1 - b];
+  }
+#pragma unroll
+  for (int ra = 0; ra < A / 2; ++ra) {
+    double se = 0.0, so = 0.0;
+#pragma unroll
+    for (int b = 0; b < HB; ++b) {
+      se += TE[ra * HB + b] * xe[b];
+      so += TO[ra * HB + b] * xo[b];
+    }
+    if constexpr (B % 2 == 1) se += TM[ra] * x[B / 2];
+    y[ra] = se + so;
+    y[A - 1 - ra] = SIGN > 0 ? se - so : so - se;
+  }
+  if constexpr (A % 2 == 1) {
+    constexpr int ra = A / 2;
+    double sm = 0.0;
+#pragma unroll
+    for (int b = 0; b < HB; ++b) sm += SIGN > 0 ? TE[ra * HB + b] * xe[b] : TO[ra * HB + b] * xo[b];
+    if constexpr (SIGN > 0 && B % 2 == 1) sm += TM[ra] * x[B / 2];
+    y[ra] = sm;
+  }
+}
+
+// EO tables of the generic kernel: J (Q x P1), J^T (P1 x Q), D (Q x Q), D^T (Q x Q)
+template <int P1, int Q>
+constexpr int elem_eo_tab_doubles() {
+  return EoTab<Q, P1>::SIZE + EoTab<P1, Q>::SIZE + 2 * EoTab<Q, Q>::SIZE;
+}
+
 template <int P1, int Q, bool COLLOC, int NC>
 inline int elem_per_block() {
   constexpr int QQ = Q * Q;
@@ -42,7 +115,8 @@ inline int elem_per_block() {
 template <int P1, int Q, bool COLLOC, int NC>
 inline size_t elem_smem_bytes(int eb) {
   using S = ElemShape<P1, Q, COLLOC>;
-  return sizeof(double) * (size_t(Q) * P1 + size_t(Q) * Q + size_t(eb) * S::NBUF * NC * S::Q3 + 32 * NC);
+  return sizeof(double) * (size_t(Q) * P1 + size_t(Q) * Q + elem_eo_tab_doubles<P1, Q>() +
+                           size_t(eb) * S::NBUF * NC * S::Q3 + 32 * NC);
 }
 
 // Threads of one block (whole warps); the launch bound below lets the compiler
@@ -63,7 +137,11 @@ __global__ void __launch_bounds__(elem_threads<Q, NC>()) elem_kernel(const Devic
   double* sJ = smem;            // [Q][P1]
   double* sD = sJ + Q * P1;     // [Q][Q]
   double* red = sD + Q * Q;     // 32 * NC reduction scratch
-  double* ebuf = red + 32 * NC;
+  double* tJ = red + 32 * NC;   // even-odd tables of J, J^T, D, D^T (register contractions)
+  double* tJT = tJ + EoTab<Q, P1>::SIZE;
+  double* tD = tJT + EoTab<P1, Q>::SIZE;
+  double* tDT = tD + EoTab<Q, Q>::SIZE;
+  double* ebuf = tDT + EoTab<Q, Q>::SIZE;
 
   const int tid = threadIdx.x;
   const int slot = tid / QQ, t = tid - (tid / QQ) * QQ;
@@ -73,6 +151,11 @@ __global__ void __launch_bounds__(elem_threads<Q, NC>()) elem_kernel(const Devic
 
   for (int i = tid; i < Q * P1; i += blockDim.x) sJ[i] = m.basis[i];
   for (int i = tid; i < Q * Q; i += blockDim.x) sD[i] = m.basis[2 * Q * P1 + i];
+  // read by every thread only after the barrier that follows the gather
+  eo_build<Q, P1, false>(m.basis, P1, tJ, tid, blockDim.x);
+  eo_build<P1, Q, true>(m.basis, P1, tJT, tid, blockDim.x);
+  eo_build<Q, Q, false>(m.basis + 2 * Q * P1, Q, tD, tid, blockDim.x);
+  eo_build<Q, Q, true>(m.basis + 2 * Q * P1, Q, tDT, tid, blockDim.x);
 
   double* sU = ebuf + size_t(active ? slot : 0) * S::NBUF * NC * Q3;
   double* sA = sU + NC * Q3;
@@ -134,16 +217,14 @@ __global__ void __launch_bounds__(elem_threads<Q, NC>()) elem_kernel(const Devic
     if (active) {
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
-        double col[P1];
+        double col[P1], uz[Q];
 #pragma unroll
         for (int k = 0; k < P1; ++k) col[k] = sB[c * Q3 + k * QQ + t];
+        eo_mul<Q, P1, 1>(tJ, col, uz);
 #pragma unroll
         for (int z = 0; z < Q; ++z) {
-          double s = 0.0;
-#pragma unroll
-          for (int k = 0; k < P1; ++k) s += sJ[z * P1 + k] * col[k];
-          uq[c][z] = s;
-          if constexpr (KIND == kStiff) sA[c * Q3 + z * QQ + t] = s;
+          uq[c][z] = uz[z];
+          if constexpr (KIND == kStiff) sA[c * Q3 + z * QQ + t] = uz[z];
         }
       }
     }
@@ -169,6 +250,10 @@ __global__ void __launch_bounds__(elem_threads<Q, NC>()) elem_kernel(const Devic
     double tq[NC][Q];
     if (active) {
       const double* G = a.G + e * 6 * Q3;
+      // t derivatives of the whole column first (even-odd, in registers); tq[c][z] holds u_t
+      // until the loop below overwrites it with the t component of G grad u
+#pragma unroll
+      for (int c = 0; c < NC; ++c) eo_mul<Q, Q, -1>(tD, uq[c], tq[c]);
 #pragma unroll
       for (int z = 0; z < Q; ++z) {
         const int pt = z * QQ + t;
@@ -176,12 +261,12 @@ __global__ void __launch_bounds__(elem_threads<Q, NC>()) elem_kernel(const Devic
         const double g11 = __ldcs(G + 3 * Q3 + pt), g12 = __ldcs(G + 4 * Q3 + pt), g22 = __ldcs(G + 5 * Q3 + pt);
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-          double ur = 0.0, us = 0.0, ut = 0.0;
+          double ur = 0.0, us = 0.0;
+          const double ut = tq[c][z];
 #pragma unroll
           for (int n = 0; n < Q; ++n) {
             ur += sD[tx * Q + n] * sUQ[c * Q3 + z * QQ + ty * Q + n];
             us += sD[ty * Q + n] * sUQ[c * Q3 + z * QQ + n * Q + tx];
-            ut += sD[z * Q + n] * uq[c][n];
           }
           sR[c * Q3 + pt] = g00 * ur + g01 * us + g02 * ut;
           sS[c * Q3 + pt] = g01 * ur + g11 * us + g12 * ut;
@@ -191,16 +276,18 @@ __global__ void __launch_bounds__(elem_threads<Q, NC>()) elem_kernel(const Devic
     }
     __syncthreads();
     if (active) {
+      // t part of the transpose for the whole column (even-odd, in registers)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) eo_mul<Q, Q, -1>(tDT, tq[c], vq[c]);
 #pragma unroll
       for (int z = 0; z < Q; ++z) {
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-          double v = 0.0;
+          double v = vq[c][z];
 #pragma unroll
           for (int n = 0; n < Q; ++n) {
             v += sD[n * Q + tx] * sR[c * Q3 + z * QQ + ty * Q + n];
             v += sD[n * Q + ty] * sS[c * Q3 + z * QQ + n * Q + tx];
-            v += sD[n * Q + z] * tq[c][n];
           }
           vq[c][z] = v;
         }
@@ -240,14 +327,12 @@ __global__ void __launch_bounds__(elem_threads<Q, NC>()) elem_kernel(const Devic
     // stage z^T: T2[k][qy][qx] = sum_qz J[qz][k] v(qx, qy, qz)
     if (active) {
 #pragma unroll
-      for (int c = 0; c < NC; ++c)
+      for (int c = 0; c < NC; ++c) {
+        double wk[P1];
+        eo_mul<P1, Q, 1>(tJT, vq[c], wk);
 #pragma unroll
-        for (int k = 0; k < P1; ++k) {
-          double s = 0.0;
-#pragma unroll
-          for (int z = 0; z < Q; ++z) s += sJ[z * P1 + k] * vq[c][z];
-          sA[c * Q3 + k * QQ + t] = s;
-        }
+        for (int k = 0; k < P1; ++k) sA[c * Q3 + k * QQ + t] = wk[k];
+      }
     }
     __syncthreads();
     // stage y^T: T1[k][j][qx] = sum_qy J[qy][j] T2[k][qy][qx]
