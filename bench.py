@@ -10,9 +10,19 @@ Jacobi diagonal) is outside the timed region, as in the paper (Sec. 3).
 
     python bench.py [--gpus N --steps K --warmup W] [--impl ours|reference]
 
+The headline arm runs native FP64 arithmetic; the line also carries the
+FP64-accurate FP32-pair arm and the recomputed-factor arm as `variants`, an n
+sweep of both arithmetics (r_max, n_0.8, t_0.8), the roofline of the element
+kernel, the end-to-end rate with host copies and the CPU oracle's rate.
+
 Under torchrun (N > 1) every rank solves its own independent problem (replicas,
 weak scaling); rank 0 prints one JSON line.  ``--impl reference`` times the
 CPU FP64 oracle on the host cores instead (a bounded sample of the workload).
+
+Other workloads (``--workload``): ``bp-sweep`` (BP1/BP3/BP5 at N = 3..15 over
+n = 1e4..1e8), ``bk-sweep`` (unassembled BK5, FP64 and pairs), ``mixed`` (BP6
+defect correction against plain PCG), ``batched`` (256 uneven BP5 problems),
+``adjoint`` (dJ/dkappa with finite-difference checks).
 """
 from __future__ import annotations
 
