@@ -62,3 +62,30 @@ def test_setup_without_gpu_fails_loudly(lib):
         pytest.skip("a GPU is present")
     with pytest.raises(RuntimeError):
         pkg.Operator.box(5, 1, 1, 1, 2)
+
+
+@pytest.mark.parametrize("bp,order,nelem,nglobal,arith,geom,status", [
+    (7, 3, 1, 64, 0, 0, pkg.EUNSUPPORTED),           # no such bake-off problem
+    (5, 0, 1, 8, 0, 0, pkg.EINVAL),                  # order below 1
+    (5, 16, 1, 8, 0, 0, pkg.EINVAL),                 # order above 15
+    (5, 3, 0, 64, 0, 0, pkg.EINVAL),                 # no elements
+    (5, 7, 1 << 22, 64, 0, 0, pkg.EINVAL),           # E p1^3 beyond 32-bit local indices
+    (5, 3, 1, 64, 5, 0, pkg.EINVAL),                 # unknown arithmetic
+    (3, 3, 1, 64, pkg.ARITH_DF64, 0, pkg.EUNSUPPORTED),  # pair arithmetic is BP5/BP6 only
+    (5, 3, 1, 64, 0, 7, pkg.EINVAL),                 # unknown geometry mode
+    (3, 3, 1, 64, 0, pkg.GEOM_RECOMPUTE, pkg.EUNSUPPORTED),  # recomputed factors are BP5/BP6 only
+    (6, 15, 1, 4096, 0, pkg.GEOM_RECOMPUTE, pkg.EUNSUPPORTED),  # BP6 tile too large at p1 = 16
+])
+def test_setup_validates_arguments_before_touching_the_device(lib, bp, order, nelem, nglobal, arith, geom, status):
+    """Setup rejects invalid or unbuilt combinations from the parameters alone, before any
+    data is read or any CUDA call is made (so this runs without a GPU)."""
+    import ctypes
+    coords = np.zeros(3 * 8, dtype=np.float64)  # never read: validation fails first
+    l2g = np.zeros(8, dtype=np.int64)
+    prm = pkg.Params(bp, order, 0, nelem, nglobal, arith, geom)
+    ctx = ctypes.c_void_p()
+    st = lib.ceedbp_setup(ctypes.byref(prm), coords.ctypes.data_as(ctypes.c_void_p),
+                          l2g.ctypes.data_as(ctypes.c_void_p), None, None, None, ctypes.byref(ctx))
+    assert st == status
+    assert not ctx.value
+    assert lib.ceedbp_last_error(None)
