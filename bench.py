@@ -22,7 +22,7 @@ CPU FP64 oracle on the host cores instead (a bounded sample of the workload).
 Other workloads (``--workload``): ``bp-sweep`` (BP1/BP3/BP5 at N = 3..15 over
 n = 1e4..1e8), ``bk-sweep`` (unassembled BK5, FP64 and pairs), ``mixed`` (BP6
 defect correction against plain PCG), ``batched`` (256 uneven BP5 problems),
-``adjoint`` (dJ/dkappa with finite-difference checks).
+``adjoint`` (dJ/dkappa with finite-difference checks), ``bp-point`` (one BP, order and size).
 """
 from __future__ import annotations
 
@@ -57,13 +57,14 @@ def parse_args():
     ap.add_argument("--no-sweep", action="store_true", help="skip the n sweep (r_max, n_0.8, t_0.8)")
     ap.add_argument("--sweep-iters", type=int, default=100)
     ap.add_argument("--mixed-e", type=int, default=48, help="elements per direction of the mixed workload")
+    ap.add_argument("--bp", type=int, default=3, help="bake-off problem of the bp-point workload")
     ap.add_argument("--df-tile", default=None,
                     help="pin the pair kernel's shape 'eb,schedule,seq' instead of the autotuner's choice")
     ap.add_argument("--geom", choices=["stored", "recompute"], default="stored",
                     help="geometric factors of the headline arm: stored, or recomputed in the element kernel")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-k", type=int, default=9, help="E = 2^k elements for the oracle sample")
-    ap.add_argument("--workload", choices=["sweep", "batched", "mixed", "adjoint", "bp-sweep", "bk-sweep"], default="sweep",
+    ap.add_argument("--workload", choices=["sweep", "batched", "mixed", "adjoint", "bp-sweep", "bk-sweep", "bp-point"], default="sweep",
                     help="sweep: BP5 n-sweep headline; batched: 256 BP5 problems batched vs one at a time; "
                          "mixed: BP6 defect correction vs FP64 PCG; adjoint: dJ/dkappa pipeline")
     return ap.parse_args()
@@ -697,8 +698,42 @@ def run_bk_sweep(args):
                       "unit": "DOFs/s", "reps": reps, "results": out}), flush=True)
 
 
+def run_bp_point(args):
+    """One point of the BP sweep: BP `--bp` at order `--order` on E = 2^k (`--k`), FP64, `--steps` fixed PCG
+    iterations in one graph; DOFs/s and the per-kernel split (element / update / direction)."""
+    import numpy as np
+    import torch
+
+    import paper_2004_06722_gb300 as pkg
+    from synth import box_dims, uniform_pm1
+    bp, N, K = args.bp, args.order, args.steps
+    dims = box_dims(args.k)
+    coords, l2g, dirichlet = pkg.mesh_box(*dims, N, 0.05)
+    op = pkg.Operator(bp, N, coords, l2g, dirichlet)
+    del coords, l2g
+    ncomp = op.ncomp
+    r = np.stack([uniform_pm1(c, np.arange(op.nglobal)) for c in range(ncomp)], axis=1)
+    rt = torch.from_numpy(np.ascontiguousarray(r if ncomp == 3 else r[:, 0])).cuda()
+    mask = torch.from_numpy(1.0 - dirichlet.astype(np.float64)).cuda() if bp not in (1, 2) else None
+    b = op.mass(rt) if bp in (1, 3, 5) else rt.clone()
+    if mask is not None:
+        b = b * (mask if ncomp == 1 else mask[:, None])
+    x = op.empty()
+    op.solve(b, x, fixed_iters=K, chunk=K)
+    for _ in range(max(3, args.warmup) // K + 1):
+        op.solve(b, x, fixed_iters=K, chunk=K)
+    ms = min(op.solve(b, x, fixed_iters=K, chunk=K)[1]["device_ms"] for _ in range(2))
+    _, pinfo = op.solve(b, x, fixed_iters=K, chunk=K, profile=True)
+    n = dims[0] * dims[1] * dims[2] * N ** 3
+    print(json.dumps({"metric": f"BP{bp} DOFs/s per CG iteration (FP64)", "unit": "DOFs/s",
+                      "value": n * ncomp * K / (ms * 1e-3), "n": n, "ncomp": ncomp, "elements": list(dims),
+                      "order": N, "steps": K, "kernel_ms": pinfo["kernel_ms"]}), flush=True)
+
+
 def main():
     args = parse_args()
+    if args.workload == "bp-point":
+        return run_bp_point(args)
     if args.workload == "bp-sweep":
         return run_bp_sweep(args)
     if args.workload == "bk-sweep":
