@@ -64,3 +64,23 @@ def test_bk_apply_rejects_wrong_shapes():
     op = pkg.Operator.box(5, 2, 1, 1, 3)
     with pytest.raises(ValueError):
         op.bk_apply(torch.zeros(2, 63, dtype=torch.float64, device="cuda"))
+
+
+@pytest.mark.parametrize("bp,N,dims", [(3, 3, (2, 1, 2)), (5, 7, (2, 1, 1)), (5, 4, (1, 2, 2)), (6, 3, (1, 2, 1))])
+def test_bk_apply_helmholtz(bp, N, dims):
+    """With ceedbp_set_helmholtz the element operator is A^e + beta B^e (Eq. (17))."""
+    beta = 3.25
+    op = pkg.Operator.box(bp, *dims, N, amp=0.05)
+    op.set_helmholtz(beta)
+    p3 = (N + 1) ** 3
+    E = dims[0] * dims[1] * dims[2]
+    shape = (E, p3) if op.ncomp == 1 else (E, p3, 3)
+    uL = uniform_pm1(5, np.arange(int(np.prod(shape)))).reshape(shape)
+    w = op.bk_apply(torch.from_numpy(uL).cuda()).cpu().numpy()
+    coords, _ = box_mesh(*dims, N, 0.05)
+    rule = bp_rule(bp, N)
+    ref = np.zeros_like(uL)
+    for e in range(E):
+        m = element_matrices(coords[e], N, rule, want=("A", "B"))
+        ref[e] = (m["A"] + beta * m["B"]) @ uL[e]
+    assert np.linalg.norm(w - ref) / np.linalg.norm(ref) < 1e-12
