@@ -424,12 +424,6 @@ cudaError_t launch_elem_df_t(const DeviceMesh& m, const ElemDfArgs& a, cudaStrea
   return launch_elem_df_s<P1, NC, false>(m, a, s);
 }
 
-template <int P1, int NC>
-inline int elem_df_blocks_t(const DeviceMesh& m) {
-  const int eb = elem_df_eb<P1, NC>(m);
-  return int((m.nelem + eb - 1) / eb);
-}
-
 // candidate shapes for the autotuner: (elements per block, staged) pairs that can run
 template <int P1, int NC>
 inline int elem_df_candidates(int* eb_out, int* stage_out, int cap) {

@@ -2,7 +2,7 @@
 // schedules; elem_dfp.cuh: pipelined sequences).  A translation unit defines
 //   CEEDBP_DF_ORDERS(X)   X(p1) for every p1 of the group
 //   CEEDBP_DF_NAME(f)     f##_<group tag>
-// and includes this file, which defines the group's launcher, block count,
+// and includes this file, which defines the group's launcher,
 // autotuner candidates and constant-bank setter; elem_df_inst.cu dispatches to
 // the group that holds an order.  Splitting the orders over translation units
 // lets nvcc compile them in parallel.
@@ -51,9 +51,6 @@ int df_candidates(int* eb, int* stage, int* ns, int cap, bool pipelined) {
 #define CEEDBP_DF_CASE(P) \
   case P:                 \
     return m.ncomp == 3 ? launch_df_any<P, 3>(m, a, s) : launch_df_any<P, 1>(m, a, s);
-#define CEEDBP_DF_BLOCKS(P) \
-  case P:                   \
-    return m.ncomp == 3 ? elem_df_blocks_t<P, 3>(m) : elem_df_blocks_t<P, 1>(m);
 #define CEEDBP_DF_CAND(P)                                                      \
   case P:                                                                      \
     return m.ncomp == 3 ? df_candidates<P, 3>(eb, stage, ns, cap, pipelined) \
@@ -78,13 +75,6 @@ cudaError_t CEEDBP_DF_NAME(launch_elem_df)(const DeviceMesh& m, const ElemDfArgs
   switch (m.p1) {
     CEEDBP_DF_ORDERS(CEEDBP_DF_CASE)
     default: return cudaErrorInvalidValue;
-  }
-}
-
-int CEEDBP_DF_NAME(elem_df_blocks)(const DeviceMesh& m) {
-  switch (m.p1) {
-    CEEDBP_DF_ORDERS(CEEDBP_DF_BLOCKS)
-    default: return 0;
   }
 }
 

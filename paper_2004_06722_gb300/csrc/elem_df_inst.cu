@@ -11,42 +11,34 @@ namespace ceedbp {
 cudaError_t set_df_dconst_a(int, const dfloat*, cudaStream_t);
 bool df_has_a(int);
 cudaError_t launch_elem_df_a(const DeviceMesh&, const ElemDfArgs&, cudaStream_t);
-int elem_df_blocks_a(const DeviceMesh&);
 int elem_df_tile_candidates_a(const DeviceMesh&, int*, int*, int*, int, bool);
 cudaError_t set_df_dconst_b(int, const dfloat*, cudaStream_t);
 bool df_has_b(int);
 cudaError_t launch_elem_df_b(const DeviceMesh&, const ElemDfArgs&, cudaStream_t);
-int elem_df_blocks_b(const DeviceMesh&);
 int elem_df_tile_candidates_b(const DeviceMesh&, int*, int*, int*, int, bool);
 cudaError_t set_df_dconst_c(int, const dfloat*, cudaStream_t);
 bool df_has_c(int);
 cudaError_t launch_elem_df_c(const DeviceMesh&, const ElemDfArgs&, cudaStream_t);
-int elem_df_blocks_c(const DeviceMesh&);
 int elem_df_tile_candidates_c(const DeviceMesh&, int*, int*, int*, int, bool);
 cudaError_t set_df_dconst_d(int, const dfloat*, cudaStream_t);
 bool df_has_d(int);
 cudaError_t launch_elem_df_d(const DeviceMesh&, const ElemDfArgs&, cudaStream_t);
-int elem_df_blocks_d(const DeviceMesh&);
 int elem_df_tile_candidates_d(const DeviceMesh&, int*, int*, int*, int, bool);
 cudaError_t set_df_dconst_e(int, const dfloat*, cudaStream_t);
 bool df_has_e(int);
 cudaError_t launch_elem_df_e(const DeviceMesh&, const ElemDfArgs&, cudaStream_t);
-int elem_df_blocks_e(const DeviceMesh&);
 int elem_df_tile_candidates_e(const DeviceMesh&, int*, int*, int*, int, bool);
 cudaError_t set_df_dconst_f(int, const dfloat*, cudaStream_t);
 bool df_has_f(int);
 cudaError_t launch_elem_df_f(const DeviceMesh&, const ElemDfArgs&, cudaStream_t);
-int elem_df_blocks_f(const DeviceMesh&);
 int elem_df_tile_candidates_f(const DeviceMesh&, int*, int*, int*, int, bool);
 cudaError_t set_df_dconst_g(int, const dfloat*, cudaStream_t);
 bool df_has_g(int);
 cudaError_t launch_elem_df_g(const DeviceMesh&, const ElemDfArgs&, cudaStream_t);
-int elem_df_blocks_g(const DeviceMesh&);
 int elem_df_tile_candidates_g(const DeviceMesh&, int*, int*, int*, int, bool);
 cudaError_t set_df_dconst_h(int, const dfloat*, cudaStream_t);
 bool df_has_h(int);
 cudaError_t launch_elem_df_h(const DeviceMesh&, const ElemDfArgs&, cudaStream_t);
-int elem_df_blocks_h(const DeviceMesh&);
 int elem_df_tile_candidates_h(const DeviceMesh&, int*, int*, int*, int, bool);
 
 cudaError_t set_df_dconst(int p1, const dfloat* host, cudaStream_t s) {
@@ -73,19 +65,6 @@ cudaError_t launch_elem_df(const DeviceMesh& m, const ElemDfArgs& a, cudaStream_
   if (df_has_g(p1)) return launch_elem_df_g(m, a, s);
   if (df_has_h(p1)) return launch_elem_df_h(m, a, s);
   return cudaErrorInvalidValue;
-}
-
-int elem_df_blocks(const DeviceMesh& m) {
-  const int p1 = m.p1;
-  if (df_has_a(p1)) return elem_df_blocks_a(m);
-  if (df_has_b(p1)) return elem_df_blocks_b(m);
-  if (df_has_c(p1)) return elem_df_blocks_c(m);
-  if (df_has_d(p1)) return elem_df_blocks_d(m);
-  if (df_has_e(p1)) return elem_df_blocks_e(m);
-  if (df_has_f(p1)) return elem_df_blocks_f(m);
-  if (df_has_g(p1)) return elem_df_blocks_g(m);
-  if (df_has_h(p1)) return elem_df_blocks_h(m);
-  return 0;
 }
 
 int elem_df_tile_candidates(const DeviceMesh& m, int* eb, int* stage, int* ns, int cap, bool pipelined) {

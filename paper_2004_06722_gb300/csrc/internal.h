@@ -136,7 +136,6 @@ cudaError_t launch_pcg_dir(const DeviceMesh& m, const double* r, double* p, cons
 // FP32-pair path (df.cuh, elem_df.cuh, pcg_df.cu).
 struct dfloat;
 struct ElemDfArgs;
-int elem_df_blocks(const DeviceMesh& m);
 int elem_df_tile_candidates(const DeviceMesh& m, int* eb, int* stage, int* ns, int cap, bool pipelined);
 cudaError_t set_df_dconst(int p1, const dfloat* host, cudaStream_t s);
 cudaError_t launch_elem_df(const DeviceMesh& m, const ElemDfArgs& a, cudaStream_t s);
