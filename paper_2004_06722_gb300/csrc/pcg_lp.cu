@@ -129,35 +129,47 @@ __global__ void inner_update_kernel(const int* __restrict__ off, const int* __re
   dfloat rz[NC], rr[NC];
 #pragma unroll
   for (int c = 0; c < NC; ++c) rz[c] = rr[c] = dfloat{0.0f, 0.0f};
-  for (int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; g < n; g += int64_t(gridDim.x) * blockDim.x) {
-    const int o0 = __ldg(off + g);
-    if (o0 < 0) continue;
-    const int o1 = __ldg(off + g + 1) & 0x7fffffff;
-    // two slots per step (their loads are independent); a node no element touches sums to 0
-    float w[NC];
+  // Two nodes per thread and step, g and g + stride: the offsets, the first local slot and its
+  // values of both nodes are loaded before either is used (most nodes -- element interiors --
+  // have exactly one slot), so two dependent load chains are in flight per thread.
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t g0 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; g0 < n; g0 += 2 * stride) {
+    int64_t gs[2] = {g0, g0 + stride};
+    int o0[2], o1[2];
+    float w[2][NC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) w[c] = 0.0f;
-    int k = o0;
-    for (; k + 1 < o1; k += 2) {
-      const int s0 = __ldg(slots + k), s1 = __ldg(slots + k + 1);
-#pragma unroll
-      for (int c = 0; c < NC; ++c) w[c] += __ldcs(wl + size_t(s0) * NC + c) + __ldcs(wl + size_t(s1) * NC + c);
+    for (int h = 0; h < 2; ++h) {
+      const bool in = gs[h] < n;
+      o0[h] = in ? __ldg(off + gs[h]) : -1;
+      o1[h] = in ? (__ldg(off + gs[h] + 1) & 0x7fffffff) : 0;
     }
-    if (k < o1) {
-      const int s0 = __ldg(slots + k);
+    int sl[2];
 #pragma unroll
-      for (int c = 0; c < NC; ++c) w[c] += __ldcs(wl + size_t(s0) * NC + c);
-    }
-    const float di = dinv[g];
+    for (int h = 0; h < 2; ++h) sl[h] = (o0[h] >= 0 && o0[h] < o1[h]) ? __ldg(slots + o0[h]) : -1;
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      if (!act[c]) continue;
-      const size_t i = size_t(g) * NC + c;
-      const float rv = fmaf(-alpha[c], w[c], r[i]);
-      x[i] = fmaf(alpha[c], lp_get(p + i), x[i]);
-      r[i] = rv;
-      acc_prod(rz[c], rv, di * rv);
-      acc_prod(rr[c], rv, rv);
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) w[h][c] = sl[h] >= 0 ? __ldcs(wl + size_t(sl[h]) * NC + c) : 0.0f;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (o0[h] < 0) continue;  // Dirichlet node (or past the end)
+      for (int k = o0[h] + 1; k < o1[h]; ++k) {
+        const int s = __ldg(slots + k);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) w[h][c] += __ldcs(wl + size_t(s) * NC + c);
+      }
+      const int64_t g = gs[h];
+      const float di = dinv[g];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        if (!act[c]) continue;
+        const size_t i = size_t(g) * NC + c;
+        const float rv = fmaf(-alpha[c], w[h][c], r[i]);
+        x[i] = fmaf(alpha[c], lp_get(p + i), x[i]);
+        r[i] = rv;
+        acc_prod(rz[c], rv, di * rv);
+        acc_prod(rr[c], rv, rv);
+      }
     }
   }
   double acc[2 * NC];
