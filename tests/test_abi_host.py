@@ -89,3 +89,18 @@ def test_setup_validates_arguments_before_touching_the_device(lib, bp, order, ne
     assert st == status
     assert not ctx.value
     assert lib.ceedbp_last_error(None)
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/ceedbp.h is a C ABI: it compiles as strict C99 (no C++ or CUDA types leak in)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_header.c"
+    src.write_text('#include "ceedbp.h"\nint main(void) { ceedbp_params p = {0}; (void)p; return 0; }\n')
+    res = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I",
+                          os.path.join(ROOT, "include"), "-c", str(src), "-o", str(tmp_path / "use_header.o")],
+                         capture_output=True, text=True)
+    assert res.returncode == 0, res.stderr
