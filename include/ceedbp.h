@@ -38,8 +38,8 @@
  *   end of every chunk of iterations to read the convergence state.
  * - Status codes are returned, never exceptions.  On any code other than
  *   CEEDBP_OK, ceedbp_last_error(ctx) describes the cause (for setup failures
- *   with ctx == NULL, ceedbp_last_error(NULL) holds the message of the
- *   calling thread's last failed setup).
+ *   with ctx == NULL, and for ceedbp_apply_noalloc, ceedbp_last_error(NULL)
+ *   holds the message of the calling thread's last such failure).
  * - Context objects are not thread-safe: one host thread at a time per ctx.
  */
 #ifndef CEEDBP_H
@@ -145,6 +145,9 @@ ceedbp_status ceedbp_setup(const ceedbp_params* params, const double* coords,
  * with the element operator of Eq. (22) (or Eq. (34)) and a deterministic
  * gather-scatter sum over sorted element slots (no floating-point atomics).
  * u_dev, w_dev: device FP64 [nglobal][ncomp]; they must not overlap.
+ * The call returns without synchronising; with CEEDBP_ARITH_DF64 a staging
+ * copy whose bounded wait gave up (the result is then invalid) is reported by
+ * the next ceedbp_check or ceedbp_solve on ctx.
  */
 ceedbp_status ceedbp_apply(ceedbp_ctx* ctx, const double* u_dev, double* w_dev);
 
@@ -221,17 +224,22 @@ ceedbp_status ceedbp_solve(ceedbp_ctx* ctx, const double* b_dev, double* x_dev,
  * operator -- e.g. while another thread holds a global-mode stream capture,
  * when another allocator owns the device memory, or in time-critical loops
  * that cannot take cudaMalloc's implicit synchronisation).
- * Computes the same w as ceedbp_apply(ctx, u_dev, w_dev), on `stream`
- * (cudaStream_t, NULL = legacy default), using for the element-local scratch
- * a file-scope device array of 32 MiB (2^22 doubles) that every GPU loading
- * the library holds until the process exits, instead of the context's buffer.
+ * Computes the same w as ceedbp_apply(ctx, u_dev, w_dev) with the same
+ * kernels (FP64 or FP32-pair arithmetic, stored or recomputed factors, kappa
+ * and the Helmholtz term as set on ctx), on `stream` (cudaStream_t, NULL =
+ * legacy default), using for the element-local scratch a file-scope device
+ * array of 32 MiB (2^22 doubles, or 2^22 pairs) instead of the context's
+ * buffer.  The array is committed on a device when ceedbp_setup first runs
+ * there (setup looks up its device address, which loads the library's device
+ * image holding it, and repeats the lookup on every later setup) and is held
+ * until the process exits.
  *   ctx    a context from ceedbp_setup (read only; its own scratch is untouched)
  *   u_dev  device FP64 [nglobal][ncomp] input, w_dev device FP64 output.
  * Limit: E * (N+1)^3 * ncomp <= 2^22 (N = 7: 8192 scalar elements); larger
- * problems return CEEDBP_EINVAL with a message on stderr and launch nothing.
- * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress with that device current); make that first call
- * before any stream capture.  All calls share the one array: calls whose
+ * problems return CEEDBP_EINVAL and launch nothing.  On any error the message
+ * is in ceedbp_last_error(NULL) of the calling thread (ctx is not modified).
+ * A pair-arithmetic staging wait that gives up is reported like one of
+ * ceedbp_apply (ceedbp_check).  All calls share the one array: calls whose
  * kernels overlap on the GPU (other streams, other threads) race on it.  Each
  * call writes every scratch entry it later reads, so nothing needs clearing.
  */
@@ -270,11 +278,13 @@ ceedbp_status ceedbp_kappa_gradient(ceedbp_ctx* ctx, const double* u_dev, const 
  * Batched BP5 solves: nprob independent problems (own mesh, order, size) set
  * up together and solved by one batched Jacobi-PCG whose every phase is one
  * launch per polynomial order for all problems, captured in CUDA graphs.
- * Arithmetic: FP64-accurate FP32 pairs (CEEDBP_ARITH_DF64); elements per
- * block per order chosen by the setup autotuner.  Each problem stops at its
- * own tolerance.
+ * Arithmetic: params[p].arith, the same for every problem (EINVAL otherwise):
+ * CEEDBP_ARITH_FP64 runs the FP64 element kernels (the even-odd kernel at odd
+ * orders) and FP64 vector kernels; CEEDBP_ARITH_DF64 the FP64-accurate FP32-
+ * pair kernels with elements per block per order chosen by the setup
+ * autotuner.  Each problem stops at its own tolerance.
  *   params[p], coords[p], l2g[p], dirichlet[p]: as for ceedbp_setup (host);
- *   params[p].bp must be 5.
+ *   params[p].bp must be 5 and params[p].geom CEEDBP_GEOM_STORED.
  * ceedbp_batch_solve: b_dev[p], x_dev[p] device FP64 [params[p].nglobal]
  * (host arrays of device pointers); opts->tol, maxit, chunk, use_graph are
  * used; infos[p] (may be NULL) receives each problem's result.
@@ -333,6 +343,38 @@ ceedbp_status ceedbp_tile_info(const ceedbp_ctx* ctx, int* elems_per_block, int*
  * CEEDBP_EUNSUPPORTED on a context without the pair path.  Synchronises the
  * context's stream and drops its captured CUDA graphs. */
 ceedbp_status ceedbp_set_tile(ceedbp_ctx* ctx, int elems_per_block, int schedule, int seq);
+
+/*
+ * Failure detection of the pair path (a service around the method; the paper
+ * has no counterpart).  The FP32-pair element kernel with the staged schedule
+ * (ceedbp_set_tile schedule 1) waits for the bulk copy of an element's G on
+ * an mbarrier with a bounded number of polls; when the wait gives up, the
+ * kernel sets a fault flag, waits once more (bounded) for its copy to land,
+ * and returns -- its results are invalid, but the CUDA context stays usable.
+ * ceedbp_check synchronises the context's stream and returns CEEDBP_ECUDA if
+ * any kernel on ctx gave up a wait since the last check (or solve), clearing
+ * the flag, or CEEDBP_ECUDA for a pending CUDA error; CEEDBP_OK otherwise.
+ * ceedbp_solve reports and clears the flag the same way at its end.
+ * ceedbp_set_wait_limit sets the number of polls of the first wait (0: give up
+ * at once, which makes every staged launch report the fault -- a test of this
+ * detection that involves no GPU fault; < 0: restore the default 2^22).  The
+ * draining wait keeps the default.  Pair contexts only (EUNSUPPORTED
+ * otherwise); synchronises the stream and drops captured graphs.
+ */
+ceedbp_status ceedbp_check(ceedbp_ctx* ctx);
+ceedbp_status ceedbp_set_wait_limit(ceedbp_ctx* ctx, int polls);
+
+/*
+ * Measured arithmetic peak of the current device (a service for the roofline
+ * of the element kernels, Sec. 8.1's empirical roofline; no counterpart in
+ * the method): FMA throughput in TFLOP/s (2 flops per FMA) of a kernel that
+ * runs 8 independent dependent FMA chains per thread on 8 blocks of 256
+ * threads per SM, in FP64 (fp64 != 0) or FP32, best of three timed launches
+ * after a warm-up (about 0.1 s each).  sm_count (may be NULL) receives the
+ * device's SM count.  Allocates and frees a small buffer; synchronises.
+ * Errors: EINVAL (tflops NULL), ECUDA (message in ceedbp_last_error(NULL)).
+ */
+ceedbp_status ceedbp_fma_peak(int fp64, double* tflops, int* sm_count);
 
 /* Release every resource owned by ctx (NULL is accepted). */
 ceedbp_status ceedbp_destroy(ceedbp_ctx* ctx);

@@ -57,26 +57,49 @@ def physical_gradients(Jinv: np.ndarray, dPhi) -> np.ndarray:
     return sum(dPhi[m][:, :, None] * Jinv[:, m, None, :] for m in range(3))
 
 
-def element_matrices(xe: np.ndarray, N: int, rule, kappa=None, want=("A", "B")):
+_TABLES: dict = {}
+
+
+def _cached_tables(N: int, points):
+    key = (N, tuple(np.asarray(points, dtype=np.float64).tolist()))
+    if key not in _TABLES:
+        if len(_TABLES) > 4:
+            _TABLES.clear()
+        _TABLES[key] = basis_tables(N, points)
+    return _TABLES[key]
+
+
+def element_matrices(xe: np.ndarray, N: int, rule, kappa=None, want=("A", "B"), rows=None):
     """Stiffness A^e and/or mass B^e of one element with nodal coordinates
     ``xe[p1^3, 3]`` under the quadrature ``rule = (points, weights)``.
-    ``kappa[Q]`` is the coefficient mu at the quadrature points (1 if None)."""
+    ``kappa[Q]`` is the coefficient mu at the quadrature points (1 if None).
+    ``rows`` (local node ids) restricts the result to those rows of the same
+    entry-by-entry sums, A^e[rows, :] and B^e[rows, :]."""
     points, weights = rule
-    Phi, dPhi = basis_tables(N, points)
+    Phi, dPhi = _cached_tables(N, points)
+    sel = slice(None) if rows is None else np.asarray(rows, dtype=np.int64)
     wq = tensor_weights(weights)
     _, detJ, Jinv = element_geometry(xe, dPhi)
     scale = wq * detJ
     out = {}
     if "A" in want:
-        grad = physical_gradients(Jinv, dPhi)
         coef = scale if kappa is None else scale * np.asarray(kappa, dtype=np.float64)
-        Ae = np.zeros((Phi.shape[1], Phi.shape[1]))
-        for d in range(3):
-            Gd = grad[:, :, d]
-            Ae += Gd.T @ (coef[:, None] * Gd)
+        if rows is None:
+            grad = physical_gradients(Jinv, dPhi)
+            Ae = np.zeros((Phi.shape[1], Phi.shape[1]))
+            for d in range(3):
+                Gd = grad[:, :, d]
+                Ae += Gd.T @ (coef[:, None] * Gd)
+        else:
+            # the same sums for the requested rows only: one physical-gradient
+            # component [Q, a] at a time instead of the whole [Q, a, 3] table
+            Ae = np.zeros((len(sel), Phi.shape[1]))
+            for d in range(3):
+                Gd = sum(dPhi[m] * Jinv[:, m, d][:, None] for m in range(3))
+                Ae += (coef[:, None] * Gd[:, sel]).T @ Gd
         out["A"] = Ae
     if "B" in want:
-        out["B"] = Phi.T @ (scale[:, None] * Phi)
+        out["B"] = Phi[:, sel].T @ (scale[:, None] * Phi)
     return out
 
 

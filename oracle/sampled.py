@@ -39,15 +39,15 @@ def sampled_rows(bp: int, Ex: int, Ey: int, Ez: int, N: int, amp: float, u_of, n
             continue
         which = "B" if (bp in (1, 2) or operator == "B") else "A"
         kap = None if kappa_of is None else kappa_of(int(elems[el]))
-        M = element_matrices(coords[el], N, rule, kappa=kap, want=(which,))[which]
+        M = element_matrices(coords[el], N, rule, kappa=kap, want=(which,), rows=hit)[which]
         ue = np.asarray(u_of(idx), dtype=np.float64)
         if dirichlet:
             bmask = _is_boundary(idx, Ex, Ey, Ez, N)
             ue = ue * (~bmask if ue.ndim == 1 else ~bmask[:, None])
         if out is None:
             out = np.zeros((len(nodes),) + ue.shape[1:])
-        for a in hit:
-            out[where[int(idx[a])]] += M[a] @ ue
+        for r, a in enumerate(hit):
+            out[where[int(idx[a])]] += M[r] @ ue
     if dirichlet:
         bmask = _is_boundary(nodes, Ex, Ey, Ez, N)
         out = out * (~bmask if out.ndim == 1 else ~bmask[:, None])

@@ -75,6 +75,9 @@ _SIGS = {
     "ceedbp_bk_apply": (ctypes.c_int, [_P, _P, _P]),
     "ceedbp_set_helmholtz": (ctypes.c_int, [_P, ctypes.c_double]),
     "ceedbp_set_tile": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "ceedbp_check": (ctypes.c_int, [_P]),
+    "ceedbp_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
+    "ceedbp_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_int]),
     "ceedbp_batch_setup": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(Params), ctypes.POINTER(_P),
                                           ctypes.POINTER(_P), ctypes.POINTER(_P), _P, ctypes.POINTER(_P)]),
     "ceedbp_batch_solve": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(SolveOpts),
@@ -125,6 +128,14 @@ def mesh_box(Ex: int, Ey: int, Ez: int, order: int, amp: float = 0.05):
     dirichlet = np.empty(ng.value, dtype=np.uint8)
     _check(lib.ceedbp_mesh_box(Ex, Ey, Ez, order, amp, _ptr(coords), _ptr(l2g), _ptr(dirichlet), None))
     return coords, l2g, dirichlet
+
+
+def fma_peak(fp64: bool = True):
+    """Measured FMA throughput of the current CUDA device: (TFLOP/s, SM count) (ceedbp_fma_peak)."""
+    lib = load_library()
+    tf, sms = ctypes.c_double(0.0), ctypes.c_int(0)
+    _check(lib.ceedbp_fma_peak(1 if fp64 else 0, ctypes.byref(tf), ctypes.byref(sms)))
+    return tf.value, sms.value
 
 
 class Operator:
@@ -215,8 +226,17 @@ class Operator:
         w = self.empty() if out is None else out
         st = self._call(lambda ctx, a, b: self.lib.ceedbp_apply_noalloc(ctx, a, b, ctypes.c_void_p(self.stream.cuda_stream)),
                         self._vec(u), self._vec(w))
-        _check(st, self.ctx)
+        _check(st, None)  # the message is the calling thread's (ceedbp_last_error(NULL))
         return w
+
+    def check(self):
+        """ceedbp_check: synchronise the operator's stream; raise CeedbpError(ECUDA) if a pair-path
+        kernel gave up a bounded staging wait since the last check or solve."""
+        _check(self.lib.ceedbp_check(self.ctx), self.ctx)
+
+    def set_wait_limit(self, polls: int):
+        """Polls of the staged pair schedule's first bounded wait (0: give up at once; < 0: default)."""
+        _check(self.lib.ceedbp_set_wait_limit(self.ctx, int(polls)), self.ctx)
 
     def bk_apply(self, uL, out=None):
         """ceedbp_bk_apply: element-local w^e = A^e u^e (or B^e u^e), uL of shape [E, p1^3] or
@@ -347,8 +367,9 @@ def kappa_misfit(kappa, op: "Operator", b, u_star, tol: float = 1e-10):
 class Batch:
     """Many independent BP5 problems solved together (ceedbp_batch_setup / _solve)."""
 
-    def __init__(self, problems, stream=None, device=None):
-        """problems: list of (order, coords, l2g, dirichlet) as returned by mesh_box."""
+    def __init__(self, problems, stream=None, device=None, arith: int = ARITH_FP64):
+        """problems: list of (order, coords, l2g, dirichlet) as returned by mesh_box; arith: the
+        arithmetic of every problem (ARITH_FP64 or ARITH_DF64)."""
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("ceedbp needs a CUDA device; there is no CPU path")
@@ -365,7 +386,7 @@ class Batch:
             l2g = np.ascontiguousarray(l2g, dtype=np.int64)
             dirichlet = np.ascontiguousarray(dirichlet, dtype=np.uint8)
             self._keep += [coords, l2g, dirichlet]
-            prm[k] = Params(5, order, 0, coords.shape[0], dirichlet.shape[0], ARITH_DF64)
+            prm[k] = Params(5, order, 0, coords.shape[0], dirichlet.shape[0], arith, GEOM_STORED)
             cp[k], lp[k], dp[k] = _ptr(coords), _ptr(l2g), _ptr(dirichlet)
             self.sizes.append((order, coords.shape[0], dirichlet.shape[0]))
         out = ctypes.c_void_p()
@@ -377,6 +398,7 @@ class Batch:
             raise CeedbpError(st, (self.lib.ceedbp_batch_last_error(None) or b"").decode())
         self.handle = out
         self.n = n
+        self.arith = arith
 
     def solve(self, bs, xs=None, tol: float = 1e-8, maxit: int = 10000, chunk: int = 32, use_graph: bool = True):
         import torch

@@ -41,6 +41,15 @@ cudaError_t launch_elem(const DeviceMesh& m, int kind, const ElemArgs& a, cudaSt
   return cudaErrorInvalidValue;
 }
 
+int elem_eo_per_block_rt(const DeviceMesh& m);
+int elem_per_block_bp5(const DeviceMesh& m);
+
+int elem_stiff_per_block(const DeviceMesh& m) {
+  if (m.X != nullptr) return 0;
+  if (use_even_odd(m)) return elem_eo_per_block_rt(m);
+  return m.colloc && m.ncomp == 1 ? elem_per_block_bp5(m) : 0;
+}
+
 int elem_blocks(const DeviceMesh& m) {
   // stiffness and mass instantiations of one (p1, q) share the block shape
   if (m.X != nullptr) return elem_rc_blocks(m);
@@ -360,6 +369,8 @@ ceedbp_status setup_impl(ceedbp_ctx* c, const double* coords, const int64_t* l2g
     CK(c, cudaStreamSynchronize(s));
     CK(c, cudaMemsetAsync(&c->d_state->fault, 0, sizeof(int), s));
   }
+  // the static scratch of ceedbp_apply_noalloc: its device address on this device, looked up here
+  CK(c, noalloc_scratch_refresh());
   CK(c, cudaStreamSynchronize(s));
   return CEEDBP_OK;
 }
@@ -367,6 +378,7 @@ ceedbp_status setup_impl(ceedbp_ctx* c, const double* coords, const int64_t* l2g
 }  // namespace
 
 namespace ceedbp {
+void set_thread_error(const std::string& msg) { g_setup_error = msg; }
 ceedbp_status setup_context(ceedbp_ctx* c, const double* coords, const int64_t* l2g, const uint8_t* dirichlet,
                             const double* kappa) {
   return setup_impl(c, coords, l2g, dirichlet, kappa);
@@ -387,6 +399,7 @@ void set_helmholtz_args(const ceedbp_ctx* c, ElemArgs& a) {
 ElemDfArgs df_args(ceedbp_ctx* c) {
   ElemDfArgs a{};
   a.fault = &c->d_state->fault;
+  a.first_wait = c->wait_polls;
   a.G = c->d_Gdf;
   a.D = c->d_Ddf;
   a.dnorm_row = c->dnorm_row;
@@ -776,7 +789,10 @@ ceedbp_status ceedbp_solve(ceedbp_ctx* c, const double* b, double* x, const ceed
   ceedbp_status result = CEEDBP_OK;
   const SolveState& h = *c->h_state;
   if (h.fault) {
-    c->err = "a kernel gave up a bounded wait for its staging copy; results are invalid";
+    c->err = "a kernel gave up a bounded wait for its staging copy (in this solve, or in an apply since the "
+             "last check); results are invalid";
+    CK(c, cudaMemsetAsync(&c->d_state->fault, 0, sizeof(int), s));
+    CK(c, cudaStreamSynchronize(s));
     return CEEDBP_ECUDA;
   }
   for (int comp = 0; comp < nc; ++comp) {
@@ -964,6 +980,32 @@ ceedbp_status ceedbp_set_tile(ceedbp_ctx* c, int eb, int schedule, int seq) {
   a.mask_in = 1;
   CK(c, launch_elem_df(c->mesh, a, s));  // one launch outside any capture (attribute setup)
   CK(c, cudaStreamSynchronize(s));
+  return CEEDBP_OK;
+}
+
+ceedbp_status ceedbp_set_wait_limit(ceedbp_ctx* c, int polls) {
+  if (!c) return fail(c, CEEDBP_EINVAL, "null context");
+  if (c->arith != CEEDBP_ARITH_DF64) return fail(c, CEEDBP_EUNSUPPORTED, "bounded waits belong to the pair path");
+  CK(c, cudaStreamSynchronize(c->stream));
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);  // captured launches hold the old limit
+  c->graphs.clear();
+  c->wait_polls = polls < 0 ? kDefaultWaitPolls : polls;
+  return CEEDBP_OK;
+}
+
+ceedbp_status ceedbp_check(ceedbp_ctx* c) {
+  if (!c) return fail(c, CEEDBP_EINVAL, "null context");
+  cudaStream_t s = c->stream;
+  CK(c, cudaStreamSynchronize(s));
+  CK(c, cudaGetLastError());
+  CK(c, cudaMemcpyAsync(&c->h_state->fault, &c->d_state->fault, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(c, cudaStreamSynchronize(s));
+  if (c->h_state->fault) {
+    CK(c, cudaMemsetAsync(&c->d_state->fault, 0, sizeof(int), s));
+    CK(c, cudaStreamSynchronize(s));
+    return fail(c, CEEDBP_ECUDA, "a kernel gave up a bounded wait for its staging copy; results since the last "
+                                 "check are invalid");
+  }
   return CEEDBP_OK;
 }
 

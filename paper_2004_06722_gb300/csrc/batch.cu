@@ -9,8 +9,10 @@
 // blocks by the last of them to finish (fixed order, no float atomics), which
 // writes that problem's alpha or beta.  Converged problems drop out (their
 // blocks return at once); an iteration chunk is one captured CUDA graph.
-// The per-order elements-per-block of the element kernel comes from the
-// setup autotuner of each group.
+// The arithmetic is that of the problems' params: native FP64 (the FP64
+// element kernels, even-odd at odd orders, with FP64 vector kernels) or
+// FP64-accurate FP32 pairs (the pipelined pair kernel, whose per-order
+// elements per block come from the setup autotuner of each group).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -129,6 +131,101 @@ __global__ void batch_dir_kernel(const int* __restrict__ off, const dfloat* __re
   }
 }
 
+// ---- FP64 arithmetic: the same three phases on double vectors
+__global__ void batch_init64_kernel(const int* __restrict__ off, const double* __restrict__ bcat,
+                                    double* __restrict__ x, double* __restrict__ r, double* __restrict__ p,
+                                    const double* __restrict__ dinv, VecTable vt, double* partials,
+                                    BatchScalars* bst, BatchGlobal* glob, double tol) {
+  __shared__ double red[32 * 3];
+  const int pr = vt.prob[blockIdx.x];
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int g = vt.n0[blockIdx.x] + threadIdx.x; g < vt.n1[blockIdx.x]; g += blockDim.x) {
+    const bool dir = __ldg(off + g) < 0;
+    const double bv = dir ? 0.0 : bcat[g];
+    const double zv = dinv[g] * bv;
+    x[g] = 0.0;
+    r[g] = bv;
+    p[g] = zv;
+    acc[0] += bv * zv;
+    acc[1] += bv * bv;
+    acc[2] += bv * bv;
+  }
+  const int b0 = vt.blk0[pr];
+  if (grid_sum_last<3>(acc, partials + 3 * size_t(b0), vt.nblk[pr], int(blockIdx.x) - b0,
+                       &bst[pr].ticket[kTicketInit], red)) {
+    if (threadIdx.x == 0) {
+      CompScalars& cs = bst[pr].c;
+      cs.rz = acc[0];
+      cs.rr = acc[1];
+      cs.bb = acc[2];
+      cs.tol2 = tol * tol * cs.bb;
+      cs.alpha = cs.beta = cs.pAp = 0.0;
+      cs.iters = 0;
+      cs.status = isfinite(cs.rz) && isfinite(cs.rr) ? CEEDBP_OK : CEEDBP_EBREAKDOWN;
+      cs.active = cs.status == CEEDBP_OK && cs.rr > cs.tol2 ? 1 : 0;
+      if (cs.active) atomicAdd(&glob->active_count, 1);
+    }
+  }
+}
+
+__global__ void batch_update64_kernel(const int* __restrict__ off, const int* __restrict__ slots,
+                                      const double* __restrict__ wl, double* __restrict__ x,
+                                      double* __restrict__ r, const double* __restrict__ p,
+                                      const double* __restrict__ dinv, VecTable vt, double* partials,
+                                      BatchScalars* bst, BatchGlobal* glob) {
+  __shared__ double red[32 * 2];
+  const int pr = vt.prob[blockIdx.x];
+  if (!bst[pr].c.active) return;
+  const double alpha = bst[pr].c.alpha;
+  double acc[2] = {0.0, 0.0};
+  for (int g = vt.n0[blockIdx.x] + threadIdx.x; g < vt.n1[blockIdx.x]; g += blockDim.x) {
+    const int o0 = __ldg(off + g);
+    if (o0 < 0) continue;
+    const int o1 = __ldg(off + g + 1) & 0x7fffffff;
+    double w = 0.0;
+    for (int k = o0; k < o1; ++k) w += wl[__ldg(slots + k)];
+    const double rv = r[g] - alpha * w;
+    x[g] += alpha * p[g];
+    r[g] = rv;
+    acc[0] += rv * dinv[g] * rv;
+    acc[1] += rv * rv;
+  }
+  const int b0 = vt.blk0[pr];
+  if (grid_sum_last<2>(acc, partials + 2 * size_t(b0), vt.nblk[pr], int(blockIdx.x) - b0,
+                       &bst[pr].ticket[kTicketUpdate], red)) {
+    if (threadIdx.x == 0) {
+      CompScalars& cs = bst[pr].c;
+      cs.beta = cs.rz != 0.0 ? acc[0] / cs.rz : 0.0;
+      cs.rz = acc[0];
+      cs.rr = acc[1];
+      cs.iters += 1;
+      if (!isfinite(acc[0])) cs.status = CEEDBP_EBREAKDOWN;
+      if (cs.rr <= cs.tol2 || cs.status != CEEDBP_OK) {
+        cs.active = 0;
+        atomicSub(&glob->active_count, 1);
+      }
+    }
+  }
+}
+
+__global__ void batch_dir64_kernel(const int* __restrict__ off, const double* __restrict__ r, double* __restrict__ p,
+                                   const double* __restrict__ dinv, VecTable vt, const BatchScalars* bst) {
+  const int pr = vt.prob[blockIdx.x];
+  if (!bst[pr].c.active) return;
+  const double beta = bst[pr].c.beta;
+  for (int g = vt.n0[blockIdx.x] + threadIdx.x; g < vt.n1[blockIdx.x]; g += blockDim.x) {
+    if (__ldg(off + g) < 0) continue;
+    p[g] = dinv[g] * r[g] + beta * p[g];
+  }
+}
+
+__global__ void batch_scatter64_kernel(const double* __restrict__ src, double* const* __restrict__ dst, VecTable vt,
+                                       const int* __restrict__ node0) {
+  const int pr = vt.prob[blockIdx.x];
+  double* d = dst[pr];
+  for (int g = vt.n0[blockIdx.x] + threadIdx.x; g < vt.n1[blockIdx.x]; g += blockDim.x) d[g - node0[pr]] = src[g];
+}
+
 // b of every problem into the concatenated vector / x back to every problem
 __global__ void batch_gather_kernel(const double* const* __restrict__ src, double* __restrict__ dst, VecTable vt,
                                     const int* __restrict__ node0) {
@@ -177,6 +274,7 @@ struct GraphChunk {
 
 struct ceedbp_batch {
   int nprob = 0;
+  int arith = CEEDBP_ARITH_DF64;
   cudaStream_t stream = nullptr;
   std::vector<BatchGroup> groups;
   std::vector<int> prob_group, prob_index;
@@ -227,6 +325,27 @@ void run_batch_iterations(ceedbp_batch* b, int n) {
   for (int it = 0; it < n; ++it)
     for (auto& g : b->groups) {
       ceedbp_ctx* c = g.ctx;
+      if (b->arith == CEEDBP_ARITH_FP64) {
+        ElemArgs a{};
+        a.u = c->d_p;
+        a.wl = c->d_wl;
+        a.G = c->d_G;
+        a.partials = g.d_part;
+        a.skip_dirichlet_out = 1;
+        a.blk_prob = g.blk_prob;
+        a.blk_e0 = g.blk_e0;
+        a.blk_n = g.blk_n;
+        a.prob_blk0 = g.prob_blk0;
+        a.prob_nblk = g.prob_nblk;
+        a.bst = g.d_bst;
+        a.batch_blocks = g.nblk_e;
+        launch_elem(c->mesh, kStiff, a, b->stream);
+        batch_update64_kernel<<<g.nblk_v, 256, 0, b->stream>>>(c->mesh.off, c->mesh.slots, c->d_wl, c->d_ax,
+                                                               c->d_r, c->d_p, c->d_dinv, g.vt, g.d_part, g.d_bst,
+                                                               b->d_glob);
+        batch_dir64_kernel<<<g.nblk_v, 256, 0, b->stream>>>(c->mesh.off, c->d_r, c->d_p, c->d_dinv, g.vt, g.d_bst);
+        continue;
+      }
       ElemDfArgs a{};
       a.u_df = reinterpret_cast<const dfloat*>(c->d_p);
       a.wl = reinterpret_cast<dfloat*>(c->d_wl);
@@ -275,8 +394,13 @@ ceedbp_status ceedbp_batch_setup(int nprob, const ceedbp_params* params, const d
     return st;
   };
   std::map<int, std::vector<int>> by_order;
+  b->arith = params[0].arith;
+  if (b->arith != CEEDBP_ARITH_FP64 && b->arith != CEEDBP_ARITH_DF64)
+    return fail_out(bfail(nullptr, CEEDBP_EINVAL, "unknown arith"));
   for (int p = 0; p < nprob; ++p) {
     if (params[p].bp != 5) return fail_out(bfail(nullptr, CEEDBP_EUNSUPPORTED, "batched solves are built for BP5"));
+    if (params[p].arith != b->arith)
+      return fail_out(bfail(nullptr, CEEDBP_EINVAL, "all problems of a batch take the same arith"));
     if (params[p].geom != CEEDBP_GEOM_STORED)
       return fail_out(bfail(nullptr, CEEDBP_EUNSUPPORTED, "batched solves use stored geometric factors"));
     if (params[p].order < 1 || params[p].order > kMaxOrder)
@@ -315,18 +439,27 @@ ceedbp_status ceedbp_batch_setup(int nprob, const ceedbp_params* params, const d
     }
     g.ctx = new (std::nothrow) ceedbp_ctx();
     if (!g.ctx) return fail_out(bfail(nullptr, CEEDBP_ENOMEM, "host allocation failed"));
-    g.ctx->prm = ceedbp_params{5, N, 0, E, ng, CEEDBP_ARITH_DF64};
+    g.ctx->prm = ceedbp_params{5, N, 0, E, ng, b->arith, CEEDBP_GEOM_STORED};
     g.ctx->stream = b->stream;
-    g.ctx->pipelined_only = true;  // large concatenated meshes: the pipelined schedule wins
+    g.ctx->pipelined_only = true;  // pair arithmetic on large concatenated meshes: the pipelined schedule wins
     ceedbp_status st = setup_context(g.ctx, cc.data(), ll.data(), dd.data(), nullptr);
     if (st != CEEDBP_OK) {
       const std::string msg = g.ctx->err;
       b->groups.push_back(g);
       return fail_out(bfail(nullptr, st, "group setup: " + msg));
     }
-    // block tables with the autotuned shape of this order: elements per block, times the
-    // sequence length of the pipelined schedule
-    const int eb = std::max(1, g.ctx->mesh.tune_eb) * (g.ctx->mesh.tune_stage == 2 ? g.ctx->mesh.tune_ns : 1);
+    // block tables: elements per block of the FP64 kernel, or the autotuned shape of the pair
+    // kernel at this order (elements per block, times the sequence length of the pipelined schedule)
+    int eb = 0;
+    if (b->arith == CEEDBP_ARITH_FP64) {
+      eb = elem_stiff_per_block(g.ctx->mesh);
+      if (eb < 1) {
+        b->groups.push_back(g);
+        return fail_out(bfail(nullptr, CEEDBP_EUNSUPPORTED, "no FP64 batched element kernel at this order"));
+      }
+    } else {
+      eb = std::max(1, g.ctx->mesh.tune_eb) * (g.ctx->mesh.tune_stage == 2 ? g.ctx->mesh.tune_ns : 1);
+    }
     std::vector<int> bp, be0, bn, pb0, pnb, vp, vn0, vn1, vb0, vnb, n0;
     eo = 0;
     for (size_t k = 0; k < g.members.size(); ++k) {
@@ -406,9 +539,13 @@ ceedbp_status ceedbp_batch_solve(ceedbp_batch* b, const double* const* b_dev, do
     BCK(b, cudaMemcpyAsync(g.d_dst, dst.data(), sizeof(double*) * dst.size(), cudaMemcpyHostToDevice, s));
     batch_gather_kernel<<<g.nblk_v, 256, 0, s>>>(g.d_src, g.d_bcat, g.vt, g.d_node0);
     ceedbp_ctx* c = g.ctx;
-    batch_init_kernel<<<g.nblk_v, 256, 0, s>>>(c->mesh.off, g.d_bcat, reinterpret_cast<dfloat*>(c->d_ax),
-                                               reinterpret_cast<dfloat*>(c->d_r), reinterpret_cast<dfloat*>(c->d_p),
-                                               c->d_dinvdf, g.vt, g.d_part, g.d_bst, b->d_glob, o.tol);
+    if (b->arith == CEEDBP_ARITH_FP64)
+      batch_init64_kernel<<<g.nblk_v, 256, 0, s>>>(c->mesh.off, g.d_bcat, c->d_ax, c->d_r, c->d_p, c->d_dinv, g.vt,
+                                                   g.d_part, g.d_bst, b->d_glob, o.tol);
+    else
+      batch_init_kernel<<<g.nblk_v, 256, 0, s>>>(c->mesh.off, g.d_bcat, reinterpret_cast<dfloat*>(c->d_ax),
+                                                 reinterpret_cast<dfloat*>(c->d_r), reinterpret_cast<dfloat*>(c->d_p),
+                                                 c->d_dinvdf, g.vt, g.d_part, g.d_bst, b->d_glob, o.tol);
   }
   BCK(b, cudaGetLastError());
   const bool graphs = o.use_graph && s != nullptr;
@@ -444,9 +581,13 @@ ceedbp_status ceedbp_batch_solve(ceedbp_batch* b, const double* const* b_dev, do
     if (b->h_glob->fault) return bfail(b, CEEDBP_ECUDA, "a kernel gave up a bounded wait; results are invalid");
   }
   if (done == 0) BCK(b, cudaEventRecord(b->ev1, s));
-  for (auto& g : b->groups)
-    batch_scatter_kernel<<<g.nblk_v, 256, 0, s>>>(reinterpret_cast<const dfloat*>(g.ctx->d_ax), g.d_dst, g.vt,
-                                                  g.d_node0);
+  for (auto& g : b->groups) {
+    if (b->arith == CEEDBP_ARITH_FP64)
+      batch_scatter64_kernel<<<g.nblk_v, 256, 0, s>>>(g.ctx->d_ax, g.d_dst, g.vt, g.d_node0);
+    else
+      batch_scatter_kernel<<<g.nblk_v, 256, 0, s>>>(reinterpret_cast<const dfloat*>(g.ctx->d_ax), g.d_dst, g.vt,
+                                                    g.d_node0);
+  }
   BCK(b, cudaGetLastError());
   BCK(b, cudaStreamSynchronize(s));
   float ms = 0.0f;

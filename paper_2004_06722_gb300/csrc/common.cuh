@@ -72,4 +72,26 @@ __device__ __forceinline__ bool grid_sum_last(double (&v)[NV], double* partials,
   return true;
 }
 
+// Batched solves: the blocks of one problem form a contiguous range starting at
+// prob_blk0[prob]; that problem's (p, A p) is summed over its own blocks by the
+// last of them to finish (fixed order), which writes the problem's alpha.
+__device__ __forceinline__ void batch_alpha(double (&dot)[1], double* partials, const int* prob_blk0,
+                                            const int* prob_nblk, BatchScalars* bst, int prob, double* red) {
+  const int b0 = prob_blk0[prob];
+  if (grid_sum_last<1>(dot, partials + b0, prob_nblk[prob], int(blockIdx.x) - b0, &bst[prob].ticket[kTicketApply],
+                       red)) {
+    if (threadIdx.x == 0) {
+      CompScalars& cs = bst[prob].c;
+      const double pAp = dot[0];
+      cs.pAp = pAp;
+      if (!(pAp > 0.0) || !isfinite(pAp) || !isfinite(cs.rz)) {
+        cs.status = CEEDBP_EBREAKDOWN;
+        cs.alpha = 0.0;
+      } else {
+        cs.alpha = cs.rz / pAp;
+      }
+    }
+  }
+}
+
 }  // namespace ceedbp

@@ -6,6 +6,7 @@
 
 #include "df.cuh"
 #include "internal.h"
+#include "kernel_args.h"
 
 struct GraphEntry {
   double* x;
@@ -45,6 +46,7 @@ struct ceedbp_ctx {
   ceedbp::dfloat* d_Ddf = nullptr;
   ceedbp::dfloat* d_dinvdf = nullptr;
   float dnorm_row = 0.0f, dnorm_col = 0.0f;
+  int wait_polls = ceedbp::kDefaultWaitPolls;  // first bounded wait of the staged pair schedule
   // defect correction: low-precision G copies, FP32 inner vectors, outer norms
   float* d_G32 = nullptr;
   void* d_Gbf = nullptr;

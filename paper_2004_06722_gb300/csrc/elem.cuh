@@ -146,8 +146,17 @@ __global__ void __launch_bounds__(elem_threads<Q, NC>()) elem_kernel(const Devic
   const int tid = threadIdx.x;
   const int slot = tid / QQ, t = tid - (tid / QQ) * QQ;
   const int tx = t % Q, ty = t / Q;
-  const int64_t e = int64_t(blockIdx.x) * eb + slot;
-  const bool active = slot < eb && e < m.nelem;
+  int64_t e0 = int64_t(blockIdx.x) * eb;
+  int nact = m.nelem - e0 < eb ? int(m.nelem - e0) : eb;
+  int prob = 0;
+  if (a.blk_prob != nullptr) {  // batched: this block holds elements of one problem
+    prob = a.blk_prob[blockIdx.x];
+    if (!a.bst[prob].c.active) return;
+    e0 = a.blk_e0[blockIdx.x];
+    nact = a.blk_n[blockIdx.x];
+  }
+  const int64_t e = e0 + slot;
+  const bool active = slot < nact;
 
   for (int i = tid; i < Q * P1; i += blockDim.x) sJ[i] = m.basis[i];
   for (int i = tid; i < Q * Q; i += blockDim.x) sD[i] = m.basis[2 * Q * P1 + i];
@@ -366,6 +375,12 @@ __global__ void __launch_bounds__(elem_threads<Q, NC>()) elem_kernel(const Devic
     }
   }
 
+  if constexpr (NC == 1) {
+    if (a.blk_prob != nullptr) {  // per-problem alpha from a segmented last-block reduction
+      batch_alpha(dot, a.partials, a.prob_blk0, a.prob_nblk, a.bst, prob, red);
+      return;
+    }
+  }
   if (a.partials != nullptr) {
     if (grid_sum_last<NC>(dot, a.partials, gridDim.x, blockIdx.x, &a.state->ticket[kTicketApply], red)) {
       if (threadIdx.x == 0) {
@@ -402,7 +417,7 @@ cudaError_t launch_elem_t(const DeviceMesh& m, const ElemArgs& a, cudaStream_t s
   // set once per instantiation (not a stream operation; kept out of graph capture)
   static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (attr != cudaSuccess) return attr;
-  const int64_t blocks = (m.nelem + eb - 1) / eb;
+  const int64_t blocks = a.blk_prob != nullptr ? int64_t(a.batch_blocks) : (m.nelem + eb - 1) / eb;
   kern<<<unsigned(blocks), nthreads, smem, s>>>(m, a, eb);
   return cudaGetLastError();
 }

@@ -85,7 +85,7 @@ __device__ __forceinline__ void slot_max(unsigned* dst, float v, bool active) {
   }
 }
 
-constexpr int kMbarPolls = 1 << 22;
+constexpr int kMbarPolls = kDefaultWaitPolls;
 
 // Register cap: for p1 <= 8 (one component) keep two 256-thread (or four 128-thread) blocks per SM.
 template <int P1, int NC, bool STAGE>
@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(P1 <= 8 ? 256 : 1024, (P1 <= 8 && NC == 1) ? 2
   }
   slot_max<PP>(&smax[slot], mx, active);
   bool staged = true;
-  if constexpr (S::STAGE_G) staged = mbar_wait(bar, 0, kMbarPolls);
+  if constexpr (S::STAGE_G) staged = mbar_wait(bar, 0, a.first_wait);
   __syncthreads();
   const float sig1 = splitter(a.dnorm_row * __uint_as_float(smax[slot]));
 

@@ -65,8 +65,17 @@ __global__ void elem_eo_kernel(const DeviceMesh m, const ElemArgs a, const int e
   const int tid = threadIdx.x;
   const int slot = tid / H3, o = tid - slot * H3;
   const int i = o % H, j = (o / H) % H, k = o / (H * H);
-  const int64_t e = int64_t(blockIdx.x) * eb + slot;
-  const bool active = slot < eb && e < m.nelem;
+  int64_t e0 = int64_t(blockIdx.x) * eb;
+  int nact = m.nelem - e0 < eb ? int(m.nelem - e0) : eb;
+  int prob = 0;
+  if (a.blk_prob != nullptr) {  // batched: this block holds elements of one problem
+    prob = a.blk_prob[blockIdx.x];
+    if (!a.bst[prob].c.active) return;
+    e0 = a.blk_e0[blockIdx.x];
+    nact = a.blk_n[blockIdx.x];
+  }
+  const int64_t e = e0 + slot;
+  const bool active = slot < nact;
 
   // E, O of D and of D^T from the FP64 derivative table Dq [P1][P1]
   const double* D = m.basis + 2 * P1 * P1;
@@ -294,6 +303,12 @@ __global__ void elem_eo_kernel(const DeviceMesh m, const ElemArgs a, const int e
     }
   }
 
+  if constexpr (NC == 1) {
+    if (a.blk_prob != nullptr) {  // per-problem alpha from a segmented last-block reduction
+      batch_alpha(dot, a.partials, a.prob_blk0, a.prob_nblk, a.bst, prob, red);
+      return;
+    }
+  }
   if (a.partials != nullptr) {
     if (grid_sum_last<NC>(dot, a.partials, gridDim.x, blockIdx.x, &a.state->ticket[kTicketApply], red)) {
       if (threadIdx.x == 0) {
@@ -328,7 +343,7 @@ cudaError_t launch_elem_eo_h(const DeviceMesh& m, const ElemArgs& a, cudaStream_
   auto kern = elem_eo_kernel<P1, NC, HELM>;
   static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (attr != cudaSuccess) return attr;
-  const int64_t blocks = (m.nelem + eb - 1) / eb;
+  const int64_t blocks = a.blk_prob != nullptr ? int64_t(a.batch_blocks) : (m.nelem + eb - 1) / eb;
   kern<<<unsigned(blocks), nthreads, smem, s>>>(m, a, eb);
   return cudaGetLastError();
 }

@@ -24,6 +24,17 @@ int elem_eo_blocks(const DeviceMesh& m) {
   }
 }
 
+#define CEEDBP_EO_EB(P) \
+  case P: return m.ncomp == 3 ? elem_eo_per_block<P, 3>() : elem_eo_per_block<P, 1>();
+
+int elem_eo_per_block_rt(const DeviceMesh& m) {
+  switch (m.p1) {
+    CEEDBP_EO_EB(2) CEEDBP_EO_EB(4) CEEDBP_EO_EB(6) CEEDBP_EO_EB(8)
+    CEEDBP_EO_EB(10) CEEDBP_EO_EB(12) CEEDBP_EO_EB(14) CEEDBP_EO_EB(16)
+    default: return 0;
+  }
+}
+
 #define CEEDBP_EO_OK(P) \
   case P: return m.ncomp == 3 ? elem_eo_launchable<P, 3>() : elem_eo_launchable<P, 1>();
 

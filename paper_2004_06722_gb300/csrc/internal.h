@@ -84,6 +84,12 @@ struct DeviceMesh {
   const double* X;      // [E][3][p1^3] nodal coordinates when the factors are recomputed, else nullptr
 };
 
+// Message of the calling thread's last failure outside a context (ceedbp_last_error(NULL)).
+void set_thread_error(const std::string& msg);
+// Looks up (again) the device address of the static scratch of ceedbp_apply_noalloc on the
+// current device; called by setup.
+cudaError_t noalloc_scratch_refresh();
+
 // ---- kernel launchers (one translation unit per family) ----------------------
 // Geometric factors G[e][6][q^3] (kappa-scaled), mass factors M[e][q^3].
 // scratch: at least geom_scratch_doubles(blocks, q) doubles.
@@ -108,8 +114,18 @@ struct ElemArgs {
   int skip_dirichlet_out;
   const double* Mq;      // Helmholtz term of Eq. (17): w += beta B u with the mass factors Mq ...
   double beta;           // ... when beta != 0 (stiffness kernels in FP64 only)
+  // batched solves (scalar problems, one problem per block, see BatchScalars); nullptr otherwise
+  const int* blk_prob;   // [nblocks] problem of each block
+  const int* blk_e0;     // [nblocks] first element of the block
+  const int* blk_n;      // [nblocks] elements in the block (<= elements per block)
+  const int* prob_blk0;  // [nprob] first block of each problem
+  const int* prob_nblk;  // [nprob] number of blocks of each problem
+  BatchScalars* bst;     // [nprob] per-problem CG scalars
+  int batch_blocks;      // grid size of a batched launch
 };
 int elem_blocks(const DeviceMesh& m);
+// Elements per block of the FP64 stiffness kernel launch_elem uses (block tables of batched solves).
+int elem_stiff_per_block(const DeviceMesh& m);
 cudaError_t launch_elem(const DeviceMesh& m, int kind, const ElemArgs& a, cudaStream_t s);
 // Stiffness element kernel recomputing G from m.X (collocated, FP64).
 cudaError_t launch_elem_rc(const DeviceMesh& m, const ElemArgs& a, cudaStream_t s);

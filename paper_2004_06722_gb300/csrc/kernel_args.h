@@ -7,6 +7,9 @@
 
 namespace ceedbp {
 
+// Polls of a bounded mbarrier wait before a kernel gives up on its staging copy.
+constexpr int kDefaultWaitPolls = 1 << 22;
+
 struct ElemDfArgs {
   const double* u_f64;   // global input in FP64 (apply), or nullptr
   const dfloat* u_df;    // global input as pairs (CG direction), or nullptr
@@ -20,6 +23,8 @@ struct ElemDfArgs {
   int mask_in;
   int skip_dirichlet_out;
   int* fault;            // set to 1 if the staging copy of G does not complete (bounded wait)
+  int first_wait = kDefaultWaitPolls;  // polls of the wait for the staged G (0: give up at once);
+                                       // the draining wait before exit always keeps the default
   // batched solves (one scalar problem per segment of blocks); nullptr otherwise
   const int* blk_prob;   // [nblocks] problem of each block
   const int* blk_e0;     // [nblocks] first element of the block

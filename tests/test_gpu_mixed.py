@@ -41,7 +41,9 @@ def test_defect_correction_reaches_fp64_tolerance(bp, N, dims, mixed, arith):
     err = np.linalg.norm(xh - x_ref) / np.linalg.norm(x_ref)
     print(f"bp{bp} N={N} mixed={mixed} arith={arith}: outer {info['outer_iters']}, inner {info['iters']}, "
           f"|x - x_oracle|/|x_oracle| = {err:.2e}")
-    assert err <= 1e-7
+    # about ten times the largest error observed on a GB300 for each inner precision
+    # (FP32 inner: 5.0e-12, BF16 storage: 2.2e-10 over these cases)
+    assert err <= (5e-11 if mixed == pkg.MIXED_FP32 else 2e-9), err
 
 
 def test_mixed_requires_prepare():

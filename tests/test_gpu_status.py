@@ -77,3 +77,54 @@ def test_argument_errors_launch_nothing():
     with pytest.raises(pkg.CeedbpError) as ei:
         p1.prepare_mixed(pkg.MIXED_FP32)
     assert ei.value.status == pkg.EUNSUPPORTED
+
+
+def _staged_shape(op):
+    """A launchable shape of the staged pair schedule (schedule 1) at this order."""
+    for eb in (1, 2, 3, 4):
+        try:
+            op.set_tile(eb, 1)
+            return eb
+        except pkg.CeedbpError:
+            continue
+    pytest.skip("no staged pair shape is launchable at this order")
+
+
+def test_bounded_wait_gives_up_and_is_reported():
+    """The staged pair schedule waits for the bulk copy of G on an mbarrier with a bounded poll
+    count.  With the limit set to 0 polls every launch gives up that wait, flags the fault, drains
+    its copy (with the default limit) and returns: the apply is reported by ceedbp_check and the
+    solve returns ECUDA.  No GPU fault is involved.  With the default restored the same context
+    applies and solves correctly again."""
+    coords, l2g, dirichlet = pkg.mesh_box(3, 3, 2, 7, 0.05)
+    op = pkg.Operator(5, 7, coords, l2g, dirichlet, arith=pkg.ARITH_DF64)
+    _staged_shape(op)
+    b = _rhs(op, dirichlet)
+    u = torch.from_numpy(uniform_pm1(4, np.arange(op.nglobal))).cuda()
+    ref = op.apply(u).clone()
+    op.check()
+    op.set_wait_limit(0)
+    op.apply(u)
+    with pytest.raises(pkg.CeedbpError) as ei:
+        op.check()
+    assert ei.value.status == pkg.ECUDA and "bounded wait" in str(ei.value)
+    op.check()  # the flag was cleared by the report
+    with pytest.raises(pkg.CeedbpError) as ei:
+        op.solve(b, tol=1e-10)
+    assert ei.value.status == pkg.ECUDA
+    op.set_wait_limit(-1)
+    w = op.apply(u)
+    op.check()
+    assert torch.equal(w, ref)
+    x, info = op.solve(b, tol=1e-10)
+    assert info["status"] == "OK" and info["rel_res"][0] <= 1e-10
+    op.close()
+
+
+def test_wait_limit_needs_pair_path():
+    op = pkg.Operator.box(5, 2, 2, 2, 3)
+    with pytest.raises(pkg.CeedbpError) as ei:
+        op.set_wait_limit(0)
+    assert ei.value.status == pkg.EUNSUPPORTED
+    op.check()  # nothing pending on an FP64 context
+    op.close()

@@ -165,3 +165,19 @@ def test_kappa_scales_stiffness():
     A1 = element_matrices(coords[0], N, rule, want=("A",))["A"]
     A2 = element_matrices(coords[0], N, rule, kappa=np.full((N + 1) ** 3, 2.5), want=("A",))["A"]
     np.testing.assert_allclose(A2, 2.5 * A1, rtol=1e-14, atol=1e-15)
+
+
+@pytest.mark.parametrize("bp,N", [(3, 3), (5, 4), (1, 2)])
+def test_row_restricted_matrices_equal_full_rows(bp, N):
+    """element_matrices(rows=...) (used for single rows of very large meshes) gives the rows
+    of the full element matrices, with and without a coefficient."""
+    coords, _ = box_mesh(2, 2, 2, N, 0.05, elements=np.array([5]))
+    rule = bp_rule(bp, N)
+    rows = [0, 3, (N + 1) ** 3 - 1, N + 2]
+    kappa = np.linspace(0.5, 2.0, len(rule[0]) ** 3)
+    for kap in (None, kappa):
+        full = element_matrices(coords[0], N, rule, kappa=kap)
+        part = element_matrices(coords[0], N, rule, kappa=kap, rows=rows)
+        for which in ("A", "B"):
+            scale = np.max(np.abs(full[which]))
+            np.testing.assert_allclose(part[which], full[which][rows], rtol=0, atol=1e-15 * scale)

@@ -155,3 +155,19 @@ def test_helmholtz_constant_mode_and_manufactured_solution(bp):
     assert np.max(np.abs(x - s)) < 2e-3
     with pytest.raises(ValueError):
         BakeoffProblem(1, 1, 1, 1, 2, beta=1.0)
+
+
+@pytest.mark.parametrize("nthreads", [1, 3, 8])
+def test_threaded_pcg_follows_the_textbook_pcg(nthreads):
+    """The multi-threaded C PCG of the CPU baseline takes the same iterates as oracle.pcg (to
+    rounding: only the order of the inner-product sums differs), for any thread count, and a
+    fixed thread count gives identical bits on repeated runs."""
+    from oracle.cpu_pcg import pcg_threads
+    prob = BakeoffProblem(5, 3, 2, 2, 4, amp=0.05)
+    b = prob.rhs(uniform_pm1(0, np.arange(prob.n_global)))[prob.free]
+    x_ref, info = pcg(prob.A_free, b, prob.diag_free, fixed_iters=25)
+    x, hist = pcg_threads(prob.A_free, b, prob.diag_free, 25, nthreads)
+    np.testing.assert_allclose(hist, info["history"], rtol=1e-9)
+    np.testing.assert_allclose(x, x_ref, rtol=0, atol=1e-11 * np.max(np.abs(x_ref)))
+    x2, hist2 = pcg_threads(prob.A_free, b, prob.diag_free, 25, nthreads)
+    assert np.array_equal(x, x2) and np.array_equal(hist, hist2)

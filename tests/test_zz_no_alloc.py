@@ -52,6 +52,54 @@ def test_noalloc_matches_apply_twice(bp, N, dims):
     op.close()
 
 
+def _twice(op, tol=APPLY_TOL):
+    shape = (op.nglobal,) if op.ncomp == 1 else (op.nglobal, 3)
+    for seed in (5, 6):  # two calls in a row, different inputs
+        u = torch.from_numpy(uniform_pm1(seed, np.arange(op.nglobal * op.ncomp)).reshape(shape)).cuda()
+        ref = op.apply(u).clone()
+        torch.cuda.synchronize()
+        w = torch.full_like(ref, float("nan"))
+        assert _noalloc(op, u, w) == pkg.OK
+        err = (torch.linalg.norm(w - ref) / torch.linalg.norm(ref)).item()
+        assert err <= tol, err
+
+
+@pytest.mark.parametrize("bp,N,dims", [(5, 7, (4, 4, 2)), (6, 3, (2, 2, 3))])
+def test_noalloc_pair_arithmetic(bp, N, dims):
+    """Contexts in FP32-pair arithmetic: the pair kernels of ceedbp_apply, with the pair scratch
+    in the same static array."""
+    op = pkg.Operator.box(bp, *dims, N, amp=0.05, arith=pkg.ARITH_DF64)
+    _twice(op)
+    op.check()
+    op.close()
+
+
+def test_noalloc_recomputed_factors():
+    op = pkg.Operator.box(5, 3, 3, 2, 5, amp=0.05, geom=pkg.GEOM_RECOMPUTE)
+    _twice(op)
+    op.close()
+
+
+def test_noalloc_helmholtz_and_kappa():
+    """A + beta B (Eq. (17)) and a variable coefficient set on the context are used too."""
+    op = pkg.Operator.box(5, 3, 2, 2, 7, amp=0.05)
+    kappa = torch.from_numpy(1.0 + 0.5 * uniform_pm1(8, np.arange(op.nelem * 8 ** 3))).cuda()
+    op.set_kappa(kappa)
+    _twice(op)
+    op.set_helmholtz(2.5)
+    _twice(op)
+    op.close()
+
+
+def test_noalloc_error_message_is_per_thread():
+    big = pkg.Operator.box(5, 16, 16, 33, 7, amp=0.05)
+    u = torch.zeros(big.nglobal, dtype=torch.float64, device="cuda")
+    with pytest.raises(pkg.CeedbpError) as ei:
+        big.apply_noalloc(u)
+    assert ei.value.status == pkg.EINVAL and "static scratch" in str(ei.value)
+    big.close()
+
+
 def test_noalloc_limit_is_exact():
     """E p1^3 = 2^22 (16 x 16 x 32 elements at N = 7) is accepted and matches
     ceedbp_apply; one more layer of elements is refused before any launch."""
