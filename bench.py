@@ -63,6 +63,9 @@ def parse_args():
     ap.add_argument("--geom", choices=["stored", "recompute"], default="stored",
                     help="geometric factors of the headline arm: stored, or recomputed in the element kernel")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the compact runs of the other configurations (BP1/BP3 points, BP6 defect "
+                         "correction, batched solves, adjoint gradient)")
     ap.add_argument("--cpu-sample-k", type=int, default=9, help="E = 2^k elements for the oracle sample")
     ap.add_argument("--workload", choices=["sweep", "batched", "mixed", "adjoint", "bp-sweep", "bk-sweep", "bp-point"], default="sweep",
                     help="sweep: BP5 n-sweep headline; batched: 256 BP5 problems batched vs one at a time; "
@@ -81,21 +84,43 @@ def load_peaks():
 
 def fp64_peak_tflops(peaks):
     """FP64 FMA peak of the GB300 derived from its unit count and clock: the nominal
-    1.25 TFLOP/s over 152 SMs at 2070 MHz is 4 flops (2 DFMA) per clock per SM."""
+    1.25 TFLOP/s over 152 SMs at 2070 MHz is 4 flops (2 DFMA) per clock per SM.  Used only
+    when the measured peak (measured_fma_peaks) is not available."""
     mhz = float(peaks.get("sm_max_mhz", 2070.0))
     return 4.0 * 152 * mhz * 1e6 / 1e12, "derived: 2 DFMA/clk/SM x 152 SMs x sm_max_mhz"
 
 
-def ncu_traffic(name: str):
-    """dram bytes per launch of a kernel from a committed ncu summary (profiles/<name>.md), else None."""
+_FMA_PEAKS = None
+
+
+def measured_fma_peaks(pkg):
+    """FP64 and FP32 FMA throughput of this GPU measured by the library's FMA-chain kernel
+    (ceedbp_fma_peak; the SM count comes from the device), measured once per process."""
+    global _FMA_PEAKS
+    if _FMA_PEAKS is None:
+        f64, sms = pkg.fma_peak(True)
+        f32, _ = pkg.fma_peak(False)
+        _FMA_PEAKS = {"fp64_tflops": f64, "fp32_tflops": f32, "sm_count": sms,
+                      "how": "ceedbp_fma_peak: 8 independent FMA chains per thread, 8 blocks of 256 threads "
+                             "per SM, best of 3 launches after a warm-up, CUDA events"}
+    return _FMA_PEAKS
+
+
+def ncu_value(name: str, key: str):
+    """A number recorded as '<key>: value' in a committed ncu summary (profiles/<name>), else None."""
     path = os.path.join(ROOT, "profiles", name)
     try:
         for line in open(path):
-            if line.startswith("dram_bytes_per_launch:"):
+            if line.startswith(key + ":"):
                 return float(line.split(":")[1])
-    except OSError:
+    except (OSError, ValueError):
         pass
     return None
+
+
+def ncu_traffic(name: str):
+    """dram bytes per launch of a kernel from a committed ncu summary (profiles/<name>.md), else None."""
+    return ncu_value(name, "dram_bytes_per_launch")
 
 
 class Clocks:
@@ -262,7 +287,8 @@ def measure(pkg, args, mesh, arith, device, rank, world, dist, geom=0):
     peaks, peak_src = load_peaks()
     rc = geom == pkg.GEOM_RECOMPUTE
     elem_bytes_dof, iter_bytes_dof, elem_flops_dof = bp5_units_recompute(N) if rc else bp5_units(N)
-    fp64_tf, fp64_src = fp64_peak_tflops(peaks)
+    fma = measured_fma_peaks(pkg)
+    fp64_tf, fp64_src = fma["fp64_tflops"], "measured: " + fma["how"]
     elem_flops = elem_flops_dof * n_dofs
     elem_bytes = elem_bytes_dof * n_dofs
     name = ("fp64rc" if rc else "fp64") if arith == pkg.ARITH_FP64 else "df64"
@@ -272,13 +298,27 @@ def measure(pkg, args, mesh, arith, device, rank, world, dist, geom=0):
         kname = "elem_rc_kernel (BK5, FP64, factors recomputed)" if rc else "elem_eo_kernel (BK5, FP64, even-odd)"
         roof = {"bound": "alu", "achieved": ach, "peak": fp64_tf, "unit": "TFLOP/s", "frac": ach / fp64_tf,
                 "traffic": traffic, "kernel": kname, "peak_source": fp64_src,
+                "peak_derived_tflops": fp64_peak_tflops(peaks)[0],
                 "hbm_frac": (elem_bytes / (elem_ms * 1e-3) / 1e9) / peaks["hbm_gbs"]}
+        # the FP64 work the kernel actually executes (ncu thread-instruction counts per element of
+        # the same kernel): DFMA counts 2 flops, DADD and DMUL 1
+        name_i = f"bk5_{'fp64rc' if rc else 'fp64'}_n{N}.md"
+        inst = [ncu_value(name_i, k) for k in ("dfma_per_element", "dadd_per_element", "dmul_per_element")]
+        if all(v is not None for v in inst):
+            E = n_dofs // N ** 3
+            exec_flops = (2 * inst[0] + inst[1] + inst[2]) * E
+            roof["executed_tflops"] = exec_flops / (elem_ms * 1e-3) / 1e12
+            roof["frac_executed"] = roof["executed_tflops"] / fp64_tf
+            roof["executed_flops_per_dof"] = exec_flops / n_dofs
+            # FP64 pipe: one DFMA, DADD or DMUL per slot, 2 slots per clock per SM (the peak's rate)
+            roof["fp64_pipe_frac"] = sum(inst) * E / (elem_ms * 1e-3) / (fp64_tf * 1e12 / 2)
     else:
         ach = elem_bytes / (elem_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / peaks["hbm_gbs"], "traffic": traffic,
                 "kernel": "elem_df_kernel (BK5, FP64-accurate FP32 pairs)", "peak_source": f"{peak_src} hbm_gbs",
-                "fp64_equiv_tflops": elem_flops / (elem_ms * 1e-3) / 1e12}
+                "fp64_equiv_tflops": elem_flops / (elem_ms * 1e-3) / 1e12,
+                "fp32_peak_measured_tflops": fma["fp32_tflops"]}
     roof.update({"elem_ms": elem_ms, "update_ms": pinfo["kernel_ms"][1], "dir_ms": pinfo["kernel_ms"][2],
                  "algorithmic_bytes_per_dof": elem_bytes_dof, "flops_per_dof": elem_flops_dof})
     out = {
@@ -346,12 +386,20 @@ def run_ours(args):
         "gpu_launches": head["gpu_launches"], "clocks": head["clocks"], "wall_s_timed": head["wall_s_timed"],
         "solver": head["solver"], "variants": variants,
     }
+    # the HBM-roofline fraction of the iteration in each arithmetic, side by side: native FP64 is
+    # bound by the FP64 pipe; the pair arithmetic carries 47-bit (not 53-bit) significands
+    line["hbm_roofline_by_arith"] = {
+        head["dtype"]: head["hbm_roofline"]["frac"],
+        **{v["dtype"] + (" recomputed factors" if k == "fp64_recompute" else ""): v["hbm_roofline"]["frac"]
+           for k, v in variants.items()}}
     del mesh
     if not args.no_sweep and rank == 0:
         line["sweep"] = run_sweep(pkg, N, args.sweep_iters, device, [head_arith] + (
             [] if args.headline_only else [pkg.ARITH_DF64 if head_arith == pkg.ARITH_FP64 else pkg.ARITH_FP64]))
+    if not args.no_extras and rank == 0 and world == 1:
+        line["configs"] = config_summaries()
     if not args.no_cpu_baseline and rank == 0 and world == 1:
-        line["cpu_baseline"] = cpu_baseline(N, args.cpu_sample_k, iters=20)
+        line["cpu_baseline"] = cpu_baseline(N, args.cpu_sample_k, iters=100)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -390,9 +438,21 @@ def run_sweep(pkg, N, iters, device, ariths):
     return out
 
 
-def cpu_baseline(N, k, iters):
-    """The oracle as it stands (assembled CSR, textbook PCG) on a bounded sample: BP5 at the same
-    order on E = 2^k elements; rate = E N^3 x iterations / PCG seconds (assembly excluded)."""
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def oracle_sample(N, k):
+    """The oracle's assembled BP5 problem on E = 2^k elements (assembly is not timed)."""
     import numpy as np
 
     from oracle.problems import BakeoffProblem
@@ -401,103 +461,130 @@ def cpu_baseline(N, k, iters):
     t0 = time.perf_counter()
     prob = BakeoffProblem(5, *dims, N, amp=0.05)
     t_setup = time.perf_counter() - t0
-    b = prob.rhs(uniform_pm1(0, np.arange(prob.n_global)))
+    b = prob.rhs(uniform_pm1(0, np.arange(prob.n_global)))[prob.free]
+    return dims, prob, b, t_setup
+
+
+def cpu_baseline(N, k, iters):
+    """The oracle as it stands (assembled CSR, textbook Jacobi PCG) on a bounded sample: BP5 at the
+    same order on E = 2^k elements, the PCG on every host core (the oracle's C PCG on POSIX threads,
+    same arithmetic as oracle/pcg.py); rate = E N^3 x iterations / PCG seconds (assembly excluded)."""
+    from oracle.cpu_pcg import host_threads, pcg_threads
+    dims, prob, b, t_setup = oracle_sample(N, k)
+    threads = host_threads()
+    pcg_threads(prob.A_free, b, prob.diag_free, 3, threads)
     t0 = time.perf_counter()
-    prob.solve(b, fixed_iters=iters)
+    pcg_threads(prob.A_free, b, prob.diag_free, iters, threads)
     t = time.perf_counter() - t0
     n = dims[0] * dims[1] * dims[2] * N ** 3
-    return {"value": n * iters / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"BP5 N={N}, E={dims[0]}x{dims[1]}x{dims[2]} (n={n}), {iters} PCG iterations on the "
-                      f"assembled CSR matrix (scipy SpMV, one thread); assembly {t_setup:.1f} s excluded",
-            "host_cpus": os.cpu_count()}
+    return {"value": n * iters / t, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"BP5 N={N}, E={dims[0]}x{dims[1]}x{dims[2]} (n={n}, CSR nnz={prob.A_free.nnz}), {iters} PCG "
+                      f"iterations of the oracle on the assembled CSR matrix, rows split over {threads} POSIX "
+                      f"threads; assembly by naive full quadrature {t_setup:.1f} s excluded",
+            "host_cpus": os.cpu_count(), "cpu_model": cpu_model()}
 
 
 def run_reference(args):
-    """The oracle timed on the host cores, one PCG iteration per step, on a bounded sample."""
-    import numpy as np
-
-    from oracle.pcg import pcg
-    from oracle.problems import BakeoffProblem
-    from synth import box_dims, uniform_pm1
+    """The oracle timed on all host cores, one PCG iteration per step, on a bounded sample."""
+    from oracle.cpu_pcg import host_threads, pcg_threads
+    from synth import box_dims
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     N, K, W = args.order, args.steps, max(3, args.warmup)
-    dims = box_dims(args.cpu_sample_k)
-    prob = BakeoffProblem(5, *dims, N, amp=0.05)
-    b = prob.rhs(uniform_pm1(0, np.arange(prob.n_global)))[prob.free]
-    pcg(prob.A_free, b, prob.diag_free, fixed_iters=W)
+    dims, prob, b, t_setup = oracle_sample(N, args.cpu_sample_k)
+    threads = host_threads()
+    pcg_threads(prob.A_free, b, prob.diag_free, W, threads)
     t0 = time.perf_counter()
-    pcg(prob.A_free, b, prob.diag_free, fixed_iters=K)
+    pcg_threads(prob.A_free, b, prob.diag_free, K, threads)
     t = time.perf_counter() - t0
     n = dims[0] * dims[1] * dims[2] * N ** 3
     big = box_dims(args.k)
     value = n * K / t
-    sample = (f"BP5 N={N}, E={dims[0]}x{dims[1]}x{dims[2]} (n={n}) instead of E=2^{args.k}; "
-              f"{K} PCG iterations of the oracle (assembled CSR, scipy SpMV, one thread)")
+    sample = (f"BP5 N={N}, E={dims[0]}x{dims[1]}x{dims[2]} (n={n}) instead of E=2^{args.k}; {K} PCG iterations "
+              f"of the oracle (assembled CSR, rows split over {threads} POSIX threads; assembly {t_setup:.1f} s "
+              f"excluded)")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": K, "warmup": W, "ms_per_step": t / K * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"BP5 FP64 Jacobi-PCG, N={N}, E={big[0]}x{big[1]}x{big[2]} deformed box",
                    "order": N},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
+                         "cpu_model": cpu_model(), "host_cpus": os.cpu_count()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
 
-def run_batched(args):
-    """256 BP5 problems (E = k^3, k log-uniform in [2, 16], N in {3, 5, 7}, amplitude U[0, 0.1]) solved
-    to 1e-8 by one batched solve, against solving them one at a time with the single-problem path."""
+def batched_summary(n_problems=256, arith_names=("fp64", "df64")):
+    """n_problems BP5 problems (E = k^3, k log-uniform in [2, 16], N in {3, 5, 7}, amplitude U[0, 0.1],
+    seed 0) solved to 1e-8 by one batched solve, against solving them one at a time with the
+    single-problem path, in each arithmetic."""
     import numpy as np
     import torch
 
     import paper_2004_06722_gb300 as pkg
     from synth import batched_problems, uniform_pm1
-    draws = batched_problems(256, seed=0)
-    probs, rhs, ops = [], [], []
-    for q in draws:
-        coords, l2g, dirichlet = pkg.mesh_box(q["k"], q["k"], q["k"], q["N"], q["amp"])
-        probs.append((q["N"], coords, l2g, dirichlet))
-        op = pkg.Operator(5, q["N"], coords, l2g, dirichlet, arith=pkg.ARITH_DF64)
-        r = torch.from_numpy(uniform_pm1(q["rhs_seed"], np.arange(op.nglobal))).cuda()
-        rhs.append(op.mass(r) * torch.from_numpy(1.0 - dirichlet.astype(np.float64)).cuda())
-        ops.append(op)
-    batch = pkg.Batch(probs)
-    for _ in range(2):
+    draws = batched_problems(n_problems, seed=0)
+    meshes = [pkg.mesh_box(q["k"], q["k"], q["k"], q["N"], q["amp"]) for q in draws]
+    out = {"problems": n_problems, "total_dofs": sum(q["k"] ** 3 * q["N"] ** 3 for q in draws),
+           "orders": {str(N): sum(1 for q in draws if q["N"] == N) for N in (3, 5, 7)}, "tol": 1e-8}
+    for name in arith_names:
+        arith = pkg.ARITH_FP64 if name == "fp64" else pkg.ARITH_DF64
+        probs, rhs, ops = [], [], []
+        for q, (coords, l2g, dirichlet) in zip(draws, meshes):
+            probs.append((q["N"], coords, l2g, dirichlet))
+            op = pkg.Operator(5, q["N"], coords, l2g, dirichlet, arith=arith)
+            r = torch.from_numpy(uniform_pm1(q["rhs_seed"], np.arange(op.nglobal))).cuda()
+            rhs.append(op.mass(r) * torch.from_numpy(1.0 - dirichlet.astype(np.float64)).cuda())
+            ops.append(op)
+        batch = pkg.Batch(probs, arith=arith)
+        for _ in range(2):
+            xs, infos = batch.solve(rhs, tol=1e-8)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         xs, infos = batch.solve(rhs, tol=1e-8)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    xs, infos = batch.solve(rhs, tol=1e-8)
-    torch.cuda.synchronize()
-    t_batch = time.perf_counter() - t0
-    for op, b in zip(ops, rhs):
-        op.solve(b, tol=1e-8)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    single = [op.solve(b, tol=1e-8)[1] for op, b in zip(ops, rhs)]
-    torch.cuda.synchronize()
-    t_seq = time.perf_counter() - t0
-    dofs_iters = sum(q["k"] ** 3 * q["N"] ** 3 * inf["iters"][0] for q, inf in zip(draws, infos))
-    diff_its = max(abs(a["iters"][0] - b["iters"][0]) for a, b in zip(infos, single))
-    print(json.dumps({"metric": "batched BP5 solve time (256 problems to 1e-8)", "value": t_batch, "unit": "s",
-                      "higher_is_better": False, "sequential_s": t_seq, "speedup": t_seq / t_batch,
-                      "dofs_iters_per_s": dofs_iters / t_batch, "max_iteration_difference": diff_its,
-                      "all_converged": all(i["status"] == "OK" for i in infos),
-                      "total_dofs": sum(q["k"] ** 3 * q["N"] ** 3 for q in draws),
-                      "orders": {str(N): sum(1 for q in draws if q["N"] == N) for N in (3, 5, 7)},
-                      "dtype": "df64 (FP32 pairs, FP64-accurate)"}), flush=True)
+        torch.cuda.synchronize()
+        t_batch = time.perf_counter() - t0
+        for op, b in zip(ops, rhs):
+            op.solve(b, tol=1e-8)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        single = [op.solve(b, tol=1e-8) for op, b in zip(ops, rhs)]
+        torch.cuda.synchronize()
+        t_seq = time.perf_counter() - t0
+        dofs_iters = sum(q["k"] ** 3 * q["N"] ** 3 * inf["iters"][0] for q, inf in zip(draws, infos))
+        diff_its = max(abs(a["iters"][0] - b[1]["iters"][0]) for a, b in zip(infos, single))
+        diff_x = max((torch.linalg.norm(x - b[0]) / torch.linalg.norm(b[0])).item() for x, b in zip(xs, single))
+        out[name] = {"batched_s": t_batch, "sequential_s": t_seq, "speedup": t_seq / t_batch,
+                     "dofs_iters_per_s": dofs_iters / t_batch, "max_iteration_difference": diff_its,
+                     "max_rel_diff_vs_single": diff_x, "all_converged": all(i["status"] == "OK" for i in infos),
+                     "dtype": "f64" if arith == pkg.ARITH_FP64 else "df64 (FP32 pairs, FP64-accurate)"}
+        batch.close()
+        for op in ops:
+            op.close()
+        del rhs, xs, single
+        torch.cuda.empty_cache()
+    return out
 
 
-def run_mixed(args):
-    """BP6 (three components), N = 7, E = 48^3 (--mixed-e), seeded RHS: plain PCG (native FP64 and FP32 pairs) against
-    FP64 defect correction with FP32 and BF16-storage inner solves, all to 1e-10 relative residual."""
+def run_batched(args):
+    """256 BP5 problems batched against one at a time, FP64 and FP32-pair arithmetic."""
+    res = batched_summary(256)
+    print(json.dumps({"metric": "batched BP5 solve time (256 problems to 1e-8)", "value": res["fp64"]["batched_s"],
+                      "unit": "s", "higher_is_better": False, "dtype": "f64", "results": res}), flush=True)
+
+
+def mixed_summary(E1, chunk=64):
+    """BP6 (three components), N = 7, E = E1^3, seeded RHS: plain PCG (native FP64 and FP32 pairs) against
+    FP64 defect correction with FP32 and BF16-storage inner solves, all to 1e-10 relative residual; the
+    difference of every solution from the native FP64 one."""
     import numpy as np
     import torch
 
     import paper_2004_06722_gb300 as pkg
     from synth import uniform_pm1
-    N, E1 = 7, args.mixed_e
+    N = 7
     coords, l2g, dirichlet = pkg.mesh_box(E1, E1, E1, N, 0.05)
     res = {}
     x_ref = None
@@ -513,7 +600,7 @@ def run_mixed(args):
         op.solve(b, tol=1e-3, mixed=mixed)  # warm-up (graphs, autotuned shapes)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        x, info = op.solve(b, tol=1e-10, mixed=mixed, chunk=64)
+        x, info = op.solve(b, tol=1e-10, mixed=mixed, chunk=chunk)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
         if x_ref is None:
@@ -525,27 +612,35 @@ def run_mixed(args):
         op.close()
         del b, x
         torch.cuda.empty_cache()
-    print(json.dumps({"metric": f"BP6 N=7 E={E1}^3 solve time to 1e-10 relative residual", "unit": "s",
-                      "higher_is_better": False, "n_per_component": E1 ** 3 * N ** 3, "results": res,
-                      "speedup_fp32_dc_vs_fp64": res["fp64_pcg"]["wall_s"] / res["fp32_defect_correction"]["wall_s"],
-                      "speedup_fp32_dc_vs_df64": res["df64_pcg"]["wall_s"] / res["fp32_defect_correction"]["wall_s"]}),
-          flush=True)
+    return {"n_per_component": E1 ** 3 * N ** 3, "elements": [E1] * 3, "results": res,
+            "speedup_fp32_dc_vs_fp64": res["fp64_pcg"]["wall_s"] / res["fp32_defect_correction"]["wall_s"],
+            "speedup_fp32_dc_vs_df64": res["df64_pcg"]["wall_s"] / res["fp32_defect_correction"]["wall_s"]}
 
 
-def run_adjoint(args):
-    """-div(kappa grad u) = f, BP5 N = 7, E = 32^3, kappa = exp(g) with 16 random Fourier modes; target u*
+def run_mixed(args):
+    """BP6 N = 7, E = 48^3 (--mixed-e): FP64 PCG against FP32 / BF16 defect correction to 1e-10."""
+    E1 = args.mixed_e
+    out = mixed_summary(E1)
+    print(json.dumps(dict({"metric": f"BP6 N=7 E={E1}^3 solve time to 1e-10 relative residual", "unit": "s",
+                           "higher_is_better": False}, **out)), flush=True)
+
+
+def adjoint_summary(E1=32, n_dirs=20, arith_name="fp64"):
+    """-div(kappa grad u) = f, BP5 N = 7, E = E1^3, kappa = exp(g) with 16 random Fourier modes; target u*
     from a second kappa; J = 1/2 ||u - u*||_B^2; dJ/dkappa by one adjoint solve and the fused gradient
-    kernel, checked by central differences (h = 1e-6) along 20 seeded directions.  Forcing f = 1."""
+    kernel, checked by central differences (h = 1e-6) along n_dirs seeded directions, in both measures:
+    the plain relative error |fd - <g,d>| / |<g,d>| and the error in the scale of the direction,
+    |fd - <g,d>| / sum |g_i d_i|.  Forcing f = 1."""
     import numpy as np
     import torch
 
     import paper_2004_06722_gb300 as pkg
-    from synth import fourier_field, fourier_modes, uniform_pm1
-    N, E1 = 7, 32
+    from synth import fourier_field, fourier_modes
+    N = 7
     coords, l2g, dirichlet = pkg.mesh_box(E1, E1, E1, N, 0.05)
     kappa = torch.from_numpy(np.exp(fourier_field(fourier_modes(0), coords))).cuda()
     kappa_star = torch.from_numpy(np.exp(fourier_field(fourier_modes(1), coords))).cuda()
-    op = pkg.Operator(5, N, coords, l2g, dirichlet, arith=pkg.ARITH_DF64 if args.arith == "df64" else pkg.ARITH_FP64)
+    op = pkg.Operator(5, N, coords, l2g, dirichlet, arith=pkg.ARITH_DF64 if arith_name == "df64" else pkg.ARITH_FP64)
     mask = torch.from_numpy(1.0 - dirichlet.astype(np.float64)).cuda()
     # smooth forcing f = 1 (b = M B 1): u and u - u* are O(1e-2), so J is well conditioned for differences
     b = op.mass(torch.ones(op.nglobal, dtype=torch.float64, device="cuda")) * mask
@@ -572,7 +667,7 @@ def run_adjoint(args):
 
     rng = np.random.default_rng(20)
     h, errs, errs13, cancel, scaled = 1e-6, [], [], [], []
-    for _ in range(20):
+    for _ in range(n_dirs):
         d = torch.from_numpy(rng.uniform(-1, 1, size=tuple(kappa.shape))).cuda()
         d /= d.abs().max()
         fd = (Jof(kappa + h * d) - Jof(kappa - h * d)) / (2 * h)
@@ -590,15 +685,21 @@ def run_adjoint(args):
         fd = (Jof(kappa + h * d * kappa) - Jof(kappa - h * d * kappa)) / (2 * h)
         ad = float((g * d * kappa).sum())
         smooth.append(abs(fd - ad) / abs(ad))
-    print(json.dumps({"metric": "adjoint gradient dJ/dkappa (forward + adjoint solve to 1e-10 + gradient)",
-                      "value": t_grad, "unit": "s", "higher_is_better": False, "J": float(J.detach()),
-                      "kappa_values": int(kappa.numel()), "n": E1 ** 3 * N ** 3,
-                      "fd_rel_err_max": max(errs), "fd_rel_err_median": float(np.median(errs)),
-                      "fd_rel_err_max_tol13": max(errs13), "fd_rel_err_median_tol13": float(np.median(errs13)),
-                      "cancellation_max": max(cancel), "fd_err_over_abs_sum_max": max(scaled),
-                      "fd_rel_err_smooth_max": max(smooth), "fd_directions": 20, "smooth_directions": 5,
-                      "h": h, "dtype": "f64" if args.arith == "fp64" else "df64 (FP32 pairs, FP64-accurate)"}),
-          flush=True)
+    op.close()
+    return {"value": t_grad, "unit": "s", "J": float(J.detach()),
+            "kappa_values": int(kappa.numel()), "n": E1 ** 3 * N ** 3, "elements": [E1] * 3,
+            "fd_rel_err_max": max(errs), "fd_rel_err_median": float(np.median(errs)),
+            "fd_rel_err_max_tol13": max(errs13), "fd_rel_err_median_tol13": float(np.median(errs13)),
+            "cancellation_max": max(cancel), "fd_err_over_abs_sum_max": max(scaled),
+            "fd_rel_err_smooth_max": max(smooth), "fd_directions": n_dirs, "smooth_directions": 5,
+            "h": h, "dtype": "f64" if arith_name == "fp64" else "df64 (FP32 pairs, FP64-accurate)"}
+
+
+def run_adjoint(args):
+    """The adjoint workload at E = 32^3 with 20 finite-difference directions."""
+    out = adjoint_summary(32, 20, args.arith)
+    print(json.dumps(dict({"metric": "adjoint gradient dJ/dkappa (forward + adjoint solve to 1e-10 + gradient)",
+                           "higher_is_better": False}, **out)), flush=True)
 
 
 def run_bp_sweep(args):
@@ -698,16 +799,15 @@ def run_bk_sweep(args):
                       "unit": "DOFs/s", "reps": reps, "results": out}), flush=True)
 
 
-def run_bp_point(args):
-    """One point of the BP sweep: BP `--bp` at order `--order` on E = 2^k (`--k`), FP64, `--steps` fixed PCG
-    iterations in one graph; DOFs/s and the per-kernel split (element / update / direction)."""
+def bp_point_summary(bp, N, k, K, warmup=3):
+    """One point of the BP sweep: BP `bp` at order N on E = 2^k, FP64, K fixed PCG iterations in one
+    graph; DOFs/s and the per-kernel split (element / update / direction)."""
     import numpy as np
     import torch
 
     import paper_2004_06722_gb300 as pkg
     from synth import box_dims, uniform_pm1
-    bp, N, K = args.bp, args.order, args.steps
-    dims = box_dims(args.k)
+    dims = box_dims(k)
     coords, l2g, dirichlet = pkg.mesh_box(*dims, N, 0.05)
     op = pkg.Operator(bp, N, coords, l2g, dirichlet)
     del coords, l2g
@@ -720,14 +820,50 @@ def run_bp_point(args):
         b = b * (mask if ncomp == 1 else mask[:, None])
     x = op.empty()
     op.solve(b, x, fixed_iters=K, chunk=K)
-    for _ in range(max(3, args.warmup) // K + 1):
+    for _ in range(max(3, warmup) // K + 1):
         op.solve(b, x, fixed_iters=K, chunk=K)
     ms = min(op.solve(b, x, fixed_iters=K, chunk=K)[1]["device_ms"] for _ in range(2))
     _, pinfo = op.solve(b, x, fixed_iters=K, chunk=K, profile=True)
+    op.close()
     n = dims[0] * dims[1] * dims[2] * N ** 3
-    print(json.dumps({"metric": f"BP{bp} DOFs/s per CG iteration (FP64)", "unit": "DOFs/s",
-                      "value": n * ncomp * K / (ms * 1e-3), "n": n, "ncomp": ncomp, "elements": list(dims),
-                      "order": N, "steps": K, "kernel_ms": pinfo["kernel_ms"]}), flush=True)
+    return {"bp": bp, "value": n * ncomp * K / (ms * 1e-3), "unit": "DOFs/s", "n": n, "ncomp": ncomp,
+            "elements": list(dims), "order": N, "steps": K, "ms_per_iter": ms / K, "kernel_ms": pinfo["kernel_ms"],
+            "dtype": "f64"}
+
+
+def run_bp_point(args):
+    """One point of the BP sweep (--bp, --order, --k, --steps)."""
+    out = bp_point_summary(args.bp, args.order, args.k, args.steps, args.warmup)
+    print(json.dumps(dict({"metric": f"BP{args.bp} DOFs/s per CG iteration (FP64)"}, **out)), flush=True)
+
+
+def config_summaries():
+    """Compact, bounded runs of the other configurations for the default bench line (about three
+    minutes): BP1 and BP3 at N = 7 on E = 2^18 (100 fixed iterations), BP6 defect correction at
+    E = 16^3, 64 batched BP5 problems (FP64 and pairs) and the adjoint gradient at E = 16^3 with 20
+    finite-difference directions."""
+    import torch
+    out = {}
+    t_all = time.perf_counter()
+    for bp in (1, 3):
+        t0 = time.perf_counter()
+        out[f"bp{bp}_n7"] = bp_point_summary(bp, 7, 18, 100)
+        out[f"bp{bp}_n7"]["wall_s"] = time.perf_counter() - t0
+        torch.cuda.empty_cache()
+    t0 = time.perf_counter()
+    out["bp6_defect_correction"] = mixed_summary(16)
+    out["bp6_defect_correction"]["wall_s"] = time.perf_counter() - t0
+    torch.cuda.empty_cache()
+    t0 = time.perf_counter()
+    out["batched"] = batched_summary(64)
+    out["batched"]["wall_s"] = time.perf_counter() - t0
+    torch.cuda.empty_cache()
+    t0 = time.perf_counter()
+    out["adjoint"] = adjoint_summary(16, 20, "fp64")
+    out["adjoint"]["wall_s"] = time.perf_counter() - t0
+    torch.cuda.empty_cache()
+    out["wall_s"] = time.perf_counter() - t_all
+    return out
 
 
 def main():

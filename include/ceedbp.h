@@ -376,6 +376,19 @@ ceedbp_status ceedbp_set_wait_limit(ceedbp_ctx* ctx, int polls);
  */
 ceedbp_status ceedbp_fma_peak(int fp64, double* tflops, int* sm_count);
 
+/*
+ * Measured throughput of warp-level MMA instructions (mma.sync) on the current
+ * device, in TFLOP/s (2 m n k flops per instruction), for kind 0: FP64
+ * m8n8k4, 1: TF32 m16n8k8 with FP32 accumulation, 2: BF16 m16n8k16 with FP32
+ * accumulation; 4 independent accumulator tiles per warp, 8 blocks of 256
+ * threads per SM, best of three timed launches after a warm-up.  The element
+ * contractions are small dense products (Sec. 5, Eqs. (29)-(33)); these
+ * rates, against ceedbp_fma_peak's, tell whether moving them to the tensor
+ * cores can pay.  Errors: EINVAL (bad kind or NULL), ECUDA (message in
+ * ceedbp_last_error(NULL)).
+ */
+ceedbp_status ceedbp_mma_peak(int kind, double* tflops);
+
 /* Release every resource owned by ctx (NULL is accepted). */
 ceedbp_status ceedbp_destroy(ceedbp_ctx* ctx);
 

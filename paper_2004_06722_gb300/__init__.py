@@ -77,6 +77,7 @@ _SIGS = {
     "ceedbp_set_tile": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "ceedbp_check": (ctypes.c_int, [_P]),
     "ceedbp_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
+    "ceedbp_mma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "ceedbp_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_int]),
     "ceedbp_batch_setup": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(Params), ctypes.POINTER(_P),
                                           ctypes.POINTER(_P), ctypes.POINTER(_P), _P, ctypes.POINTER(_P)]),
@@ -136,6 +137,14 @@ def fma_peak(fp64: bool = True):
     tf, sms = ctypes.c_double(0.0), ctypes.c_int(0)
     _check(lib.ceedbp_fma_peak(1 if fp64 else 0, ctypes.byref(tf), ctypes.byref(sms)))
     return tf.value, sms.value
+
+
+def mma_peak(kind: int) -> float:
+    """Measured mma.sync throughput in TFLOP/s: kind 0 FP64 m8n8k4, 1 TF32 m16n8k8, 2 BF16 m16n8k16."""
+    lib = load_library()
+    tf = ctypes.c_double(0.0)
+    _check(lib.ceedbp_mma_peak(int(kind), ctypes.byref(tf)))
+    return tf.value
 
 
 class Operator:

@@ -65,3 +65,14 @@ def test_ncu_traffic_reads_committed_profiles():
             v = bench.ncu_traffic(name)
             assert v is not None and 1e9 < v < 2e10, name
     assert bench.ncu_traffic("no_such_profile.md") is None
+
+
+def test_ncu_value_reads_instruction_counts(tmp_path, monkeypatch):
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "x.md").write_text("# t\n\ndfma_per_element: 12288\ndadd_per_element: 3.5e3\nother: z\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.ncu_value("x.md", "dfma_per_element") == 12288.0
+    assert bench.ncu_value("x.md", "dadd_per_element") == 3500.0
+    assert bench.ncu_value("x.md", "other") is None
+    assert bench.ncu_value("missing.md", "dfma_per_element") is None
