@@ -590,7 +590,8 @@ def mixed_summary(E1, chunk=64):
     x_ref = None
     for name, arith, mixed in [("fp64_pcg", pkg.ARITH_FP64, 0), ("df64_pcg", pkg.ARITH_DF64, 0),
                                ("fp32_defect_correction", pkg.ARITH_DF64, pkg.MIXED_FP32),
-                               ("bf16_defect_correction", pkg.ARITH_DF64, pkg.MIXED_BF16)]:
+                               ("bf16_defect_correction", pkg.ARITH_DF64, pkg.MIXED_BF16),
+                               ("fp32_tc_defect_correction", pkg.ARITH_DF64, pkg.MIXED_FP32_TC)]:
         op = pkg.Operator(6, N, coords, l2g, dirichlet, arith=arith)
         if mixed:
             op.prepare_mixed(mixed)

@@ -162,13 +162,18 @@ ceedbp_status ceedbp_mass(ceedbp_ctx* ctx, const double* u_dev, double* w_dev);
 enum {
   CEEDBP_MIXED_NONE = 0,
   CEEDBP_MIXED_FP32 = 1, /* inner operator and vectors in FP32 */
-  CEEDBP_MIXED_BF16 = 2  /* inner G and direction p stored in BF16, FP32 arithmetic */
+  CEEDBP_MIXED_BF16 = 2, /* inner G and direction p stored in BF16, FP32 arithmetic */
+  CEEDBP_MIXED_FP32_TC = 3 /* as CEEDBP_MIXED_FP32, with the element contractions of the inner
+                              operator on the tensor cores: warp-level TF32 MMAs with every
+                              operand split into two TF32 parts (3xTF32, FP32-level products);
+                              order 7 only (EUNSUPPORTED otherwise) */
 };
 
 /*
  * Prepare defect-correction solves (BP5/BP6): allocates the low-precision copy
  * of the geometric factors (FP32 or BF16, rounded to nearest from the FP64
- * factors of Eq. (23)) and the FP32 inner CG vectors.  Call once per
+ * factors of Eq. (23); CEEDBP_MIXED_FP32_TC shares the FP32 copy) and the
+ * FP32 inner CG vectors.  Call once per
  * precision before ceedbp_solve with opts->mixed = precision.
  * Errors: EUNSUPPORTED (BP1/BP3), EINVAL, ENOMEM, ECUDA.
  */

@@ -20,7 +20,7 @@ OK, EINVAL, ENOMEM, ECUDA, ENOCONV, EBREAKDOWN, EUNSUPPORTED = range(7)
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "EBREAKDOWN", 6: "EUNSUPPORTED"}
 ARITH_FP64, ARITH_DF64 = 0, 1
 GEOM_STORED, GEOM_RECOMPUTE = 0, 1
-MIXED_NONE, MIXED_FP32, MIXED_BF16 = 0, 1, 2
+MIXED_NONE, MIXED_FP32, MIXED_BF16, MIXED_FP32_TC = 0, 1, 2, 3
 
 
 class CeedbpError(RuntimeError):

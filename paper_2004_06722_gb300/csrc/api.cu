@@ -414,8 +414,10 @@ void mark(ceedbp_ctx* c, int i, bool capturing) {
   else cudaEventRecord(c->prof[i], c->stream);
 }
 
-void run_inner_iterations(ceedbp_ctx* c, int bf16, int n) {
+// inner iterations of defect correction; mode CEEDBP_MIXED_FP32, _BF16 or _FP32_TC
+void run_inner_iterations(ceedbp_ctx* c, int mode, int n) {
   const DeviceMesh& m = c->mesh;
+  const int bf16 = mode == CEEDBP_MIXED_BF16 ? 1 : 0;
   ElemLpArgs a{};
   a.u = c->d_pin;
   a.wl = reinterpret_cast<float*>(c->d_wl);
@@ -423,7 +425,8 @@ void run_inner_iterations(ceedbp_ctx* c, int bf16, int n) {
   a.partials = c->d_part_apply;
   a.state = c->d_state;
   for (int i = 0; i < n; ++i) {
-    launch_elem_lp(m, a, bf16, c->stream);
+    if (mode == CEEDBP_MIXED_FP32_TC) launch_elem_tc(m, a, c->stream);
+    else launch_elem_lp(m, a, bf16, c->stream);
     launch_inner_update(m, bf16, a.wl, c->d_xin, c->d_rin, c->d_pin, c->d_dinv32, c->d_part_vec, c->d_state,
                         c->stream);
     launch_inner_dir(m, bf16, c->d_rin, c->d_pin, c->d_dinv32, c->d_state, c->stream);
@@ -483,7 +486,7 @@ ceedbp_status graph_for(ceedbp_ctx* c, double* x, int n, int profile, cudaGraphE
   cudaGraph_t graph = nullptr;
   CK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
   if (mode == 0) run_iterations(c, x, n, profile != 0, true);
-  else run_inner_iterations(c, mode == 2, n);
+  else run_inner_iterations(c, mode, n);
   cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
   cudaGraphExec_t exec = nullptr;
@@ -502,9 +505,11 @@ ceedbp_status graph_for(ceedbp_ctx* c, double* x, int n, int profile, cudaGraphE
 ceedbp_status solve_mixed(ceedbp_ctx* c, const double* b, double* x, const ceedbp_solve_opts& o,
                           ceedbp_solve_info* info) {
   const int bf16 = o.mixed == CEEDBP_MIXED_BF16 ? 1 : 0;
-  if (o.mixed != CEEDBP_MIXED_FP32 && o.mixed != CEEDBP_MIXED_BF16) return fail(c, CEEDBP_EINVAL, "unknown mixed mode");
+  if (o.mixed != CEEDBP_MIXED_FP32 && o.mixed != CEEDBP_MIXED_BF16 && o.mixed != CEEDBP_MIXED_FP32_TC)
+    return fail(c, CEEDBP_EINVAL, "unknown mixed mode");
   if (!c->colloc) return fail(c, CEEDBP_EUNSUPPORTED, "defect correction is built for BP5 and BP6");
-  if ((bf16 && !c->d_Gbf) || (!bf16 && !c->d_G32) || !c->d_xin)
+  if ((bf16 && !c->d_Gbf) || (!bf16 && !c->d_G32) || !c->d_xin ||
+      (o.mixed == CEEDBP_MIXED_FP32_TC && !c->tc_ready))
     return fail(c, CEEDBP_EINVAL, "call ceedbp_prepare_mixed for this precision first");
   const int nc = c->ncomp;
   const int64_t n = c->prm.nglobal;
@@ -560,11 +565,11 @@ ceedbp_status solve_mixed(ceedbp_ctx* c, const double* b, double* x, const ceedb
       const int k = std::min(o.chunk, inner_maxit - its);
       if (graphs) {
         cudaGraphExec_t exec = nullptr;
-        ceedbp_status st = graph_for(c, nullptr, k, 0, &exec, bf16 ? 2 : 1);
+        ceedbp_status st = graph_for(c, nullptr, k, 0, &exec, o.mixed);
         if (st != CEEDBP_OK) return st;
         CK(c, cudaGraphLaunch(exec, s));
       } else {
-        run_inner_iterations(c, bf16, k);
+        run_inner_iterations(c, o.mixed, k);
         CK(c, cudaGetLastError());
       }
       CK(c, cudaMemcpyAsync(c->h_state, c->d_state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
@@ -613,9 +618,11 @@ extern "C" {
 
 ceedbp_status ceedbp_prepare_mixed(ceedbp_ctx* c, int precision) {
   if (!c) return fail(c, CEEDBP_EINVAL, "null context");
-  if (precision != CEEDBP_MIXED_FP32 && precision != CEEDBP_MIXED_BF16)
-    return fail(c, CEEDBP_EINVAL, "precision must be CEEDBP_MIXED_FP32 or CEEDBP_MIXED_BF16");
+  if (precision != CEEDBP_MIXED_FP32 && precision != CEEDBP_MIXED_BF16 && precision != CEEDBP_MIXED_FP32_TC)
+    return fail(c, CEEDBP_EINVAL, "precision must be CEEDBP_MIXED_FP32, _BF16 or _FP32_TC");
   if (!c->colloc) return fail(c, CEEDBP_EUNSUPPORTED, "defect correction is built for BP5 and BP6");
+  if (precision == CEEDBP_MIXED_FP32_TC && !elem_tc_supported(c->mesh))
+    return fail(c, CEEDBP_EUNSUPPORTED, "the tensor-core inner operator is built for order 7 (p1 = 8)");
   if (c->d_X) return fail(c, CEEDBP_EUNSUPPORTED, "this call needs stored geometric factors (geom = STORED)");
   if (c->beta != 0.0) return fail(c, CEEDBP_EUNSUPPORTED, "defect correction is built for beta = 0");
   const int64_t n = c->prm.nglobal, nc = c->ncomp;
@@ -630,7 +637,7 @@ ceedbp_status ceedbp_prepare_mixed(ceedbp_ctx* c, int precision) {
     CK(c, cudaMallocHost(reinterpret_cast<void**>(&c->h_outer), 3 * sizeof(double)));
     CK(c, launch_narrow(c->d_dinv, c->d_dinv32, n, 0, s));
   }
-  if (precision == CEEDBP_MIXED_FP32 && !c->d_G32) {
+  if (precision != CEEDBP_MIXED_BF16 && !c->d_G32) {
     CK(c, dalloc(&c->d_G32, size_t(ng)));
     CK(c, launch_narrow(c->d_G, c->d_G32, ng, 0, s));
   }
@@ -644,7 +651,12 @@ ceedbp_status ceedbp_prepare_mixed(ceedbp_ctx* c, int precision) {
   a.wl = reinterpret_cast<float*>(c->d_wl);
   a.G = precision == CEEDBP_MIXED_BF16 ? c->d_Gbf : static_cast<const void*>(c->d_G32);
   CK(c, cudaMemsetAsync(c->d_pin, 0, sizeof(float) * size_t(n * nc), s));
-  CK(c, launch_elem_lp(c->mesh, a, precision == CEEDBP_MIXED_BF16, s));
+  if (precision == CEEDBP_MIXED_FP32_TC) {
+    CK(c, launch_elem_tc(c->mesh, a, s));
+    c->tc_ready = true;
+  } else {
+    CK(c, launch_elem_lp(c->mesh, a, precision == CEEDBP_MIXED_BF16, s));
+  }
   CK(c, cudaStreamSynchronize(s));
   return CEEDBP_OK;
 }

@@ -12,7 +12,7 @@ struct GraphEntry {
   double* x;
   int n;
   int profile;
-  int mode;  // 0: FP64 / pair iteration, 1: FP32 inner, 2: BF16 inner
+  int mode;  // 0: FP64 / pair iteration, else the CEEDBP_MIXED_* precision of the inner iterations
   cudaGraphExec_t exec;
 };
 
@@ -56,6 +56,7 @@ struct ceedbp_ctx {
   void* d_pin = nullptr;  // n * ncomp * 4 bytes (FP32 or BF16 direction)
   double* d_outer = nullptr;
   double* h_outer = nullptr;
+  bool tc_ready = false;  // the tensor-core inner operator was prepared (CEEDBP_MIXED_FP32_TC)
   // variable coefficient: coefficient-free factors (kept when kappa is used)
   double* d_Ghat = nullptr;
   double* d_scal = nullptr;  // small device outputs (misfit)
