@@ -1,5 +1,5 @@
 // Double-float arithmetic: a value is an unevaluated pair (hi, lo) of FP32
-// numbers, hi + lo.  The GB300 issues FP32 FMAs about 60 times faster than
+// numbers, hi + lo.  The GB300 issues FP32 FMAs about 63 times faster than
 // FP64 ones, so FP64-accurate contractions run on pairs of FP32 numbers.
 //
 // Building blocks (Dekker 1971; Knuth TAOCP vol. 2; Joldes, Muller and Popescu,
