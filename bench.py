@@ -58,6 +58,7 @@ def parse_args():
     ap.add_argument("--sweep-iters", type=int, default=100)
     ap.add_argument("--mixed-e", type=int, default=48, help="elements per direction of the mixed workload")
     ap.add_argument("--bp", type=int, default=3, help="bake-off problem of the bp-point workload")
+    ap.add_argument("--bps", default="1,3,5", help="bake-off problems of the bp-sweep workload")
     ap.add_argument("--df-tile", default=None,
                     help="pin the pair kernel's shape 'eb,schedule,seq' instead of the autotuner's choice")
     ap.add_argument("--geom", choices=["stored", "recompute"], default="stored",
@@ -713,7 +714,7 @@ def run_bp_sweep(args):
     from synth import box_dims, sweep_ks, uniform_pm1
     iters = args.sweep_iters
     out = {}
-    for bp in (1, 3, 5):
+    for bp in [int(v) for v in args.bps.split(",")]:
         for N in (3, 5, 7, 9, 11, 15):
             ns, rates = [], []
             for k in sweep_ks(N):

@@ -1,12 +1,13 @@
-// Element kernel instantiations for BP1 (orders 1..15), see elem.cuh.
-#include "elem.cuh"
+// Element kernel instantiations for BP1 (orders 1..15): the even-odd kernel of
+// elem_gl.cuh (every 1D contraction in even-odd form), see also elem.cuh.
+#include "elem_gl.cuh"
 
 namespace ceedbp {
 
 #define CEEDBP_ELEM_CASE(P) \
-  case P: return launch_elem_t<P, P + 1, false, kMass, 1>(m, a, s);
+  case P: return launch_elem_gl_t<P, P + 1, kMass>(m, a, s);
 #define CEEDBP_BLOCKS_CASE(P) \
-  case P: return elem_blocks_t<P, P + 1, false, 1>(m.nelem);
+  case P: return elem_gl_blocks_t<P, P + 1>(m.nelem);
 
 cudaError_t launch_elem_bp1(const DeviceMesh& m, const ElemArgs& a, cudaStream_t s) {
   switch (m.p1) {
