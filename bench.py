@@ -801,9 +801,9 @@ def run_bk_sweep(args):
                       "unit": "DOFs/s", "reps": reps, "results": out}), flush=True)
 
 
-def bp_point_summary(bp, N, k, K, warmup=3):
-    """One point of the BP sweep: BP `bp` at order N on E = 2^k, FP64, K fixed PCG iterations in one
-    graph; DOFs/s and the per-kernel split (element / update / direction)."""
+def bp_point_summary(bp, N, k, K, warmup=3, arith_name="fp64"):
+    """One point of the BP sweep: BP `bp` at order N on E = 2^k, FP64 (or FP32 pairs), K fixed PCG
+    iterations in one graph; DOFs/s and the per-kernel split (element / update / direction)."""
     import numpy as np
     import torch
 
@@ -811,7 +811,8 @@ def bp_point_summary(bp, N, k, K, warmup=3):
     from synth import box_dims, uniform_pm1
     dims = box_dims(k)
     coords, l2g, dirichlet = pkg.mesh_box(*dims, N, 0.05)
-    op = pkg.Operator(bp, N, coords, l2g, dirichlet)
+    op = pkg.Operator(bp, N, coords, l2g, dirichlet,
+                      arith=pkg.ARITH_DF64 if arith_name == "df64" else pkg.ARITH_FP64)
     del coords, l2g
     ncomp = op.ncomp
     r = np.stack([uniform_pm1(c, np.arange(op.nglobal)) for c in range(ncomp)], axis=1)
@@ -830,28 +831,30 @@ def bp_point_summary(bp, N, k, K, warmup=3):
     n = dims[0] * dims[1] * dims[2] * N ** 3
     return {"bp": bp, "value": n * ncomp * K / (ms * 1e-3), "unit": "DOFs/s", "n": n, "ncomp": ncomp,
             "elements": list(dims), "order": N, "steps": K, "ms_per_iter": ms / K, "kernel_ms": pinfo["kernel_ms"],
-            "dtype": "f64"}
+            "dtype": "f64" if arith_name == "fp64" else "df64 (FP32 pairs, FP64-accurate)"}
 
 
 def run_bp_point(args):
     """One point of the BP sweep (--bp, --order, --k, --steps)."""
-    out = bp_point_summary(args.bp, args.order, args.k, args.steps, args.warmup)
-    print(json.dumps(dict({"metric": f"BP{args.bp} DOFs/s per CG iteration (FP64)"}, **out)), flush=True)
+    out = bp_point_summary(args.bp, args.order, args.k, args.steps, args.warmup, args.arith)
+    print(json.dumps(dict({"metric": f"BP{args.bp} DOFs/s per CG iteration ({args.arith})"}, **out)), flush=True)
 
 
 def config_summaries():
     """Compact, bounded runs of the other configurations for the default bench line (about three
-    minutes): BP1 and BP3 at N = 7 on E = 2^18 (100 fixed iterations), BP6 defect correction at
-    E = 16^3, 64 batched BP5 problems (FP64 and pairs) and the adjoint gradient at E = 16^3 with 20
-    finite-difference directions."""
+    minutes): BP1 and BP3 at N = 7 on E = 2^18 (100 fixed iterations, FP64 and FP32 pairs), BP6
+    defect correction at E = 16^3, 64 batched BP5 problems (FP64 and pairs) and the adjoint gradient
+    at E = 16^3 with 20 finite-difference directions."""
     import torch
     out = {}
     t_all = time.perf_counter()
     for bp in (1, 3):
-        t0 = time.perf_counter()
-        out[f"bp{bp}_n7"] = bp_point_summary(bp, 7, 18, 100)
-        out[f"bp{bp}_n7"]["wall_s"] = time.perf_counter() - t0
-        torch.cuda.empty_cache()
+        for arith in ("fp64", "df64"):
+            key = f"bp{bp}_n7" + ("" if arith == "fp64" else "_df64")
+            t0 = time.perf_counter()
+            out[key] = bp_point_summary(bp, 7, 18, 100, arith_name=arith)
+            out[key]["wall_s"] = time.perf_counter() - t0
+            torch.cuda.empty_cache()
     t0 = time.perf_counter()
     out["bp6_defect_correction"] = mixed_summary(16)
     out["bp6_defect_correction"]["wall_s"] = time.perf_counter() - t0

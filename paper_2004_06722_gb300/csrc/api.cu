@@ -132,8 +132,9 @@ ceedbp_status setup_impl(ceedbp_ctx* c, const double* coords, const int64_t* l2g
     return fail(c, CEEDBP_EINVAL, "problem too large for 32-bit local indices (E p1^3 and nglobal must stay below 2^31)");
   const bool masked = P.bp != 1 && P.bp != 2 && dirichlet != nullptr;
   if (P.arith != CEEDBP_ARITH_FP64 && P.arith != CEEDBP_ARITH_DF64) return fail(c, CEEDBP_EINVAL, "unknown arith");
-  if (P.arith == CEEDBP_ARITH_DF64 && !gll_quad)
-    return fail(c, CEEDBP_EUNSUPPORTED, "the FP32-pair arithmetic is built for BP5 and BP6 only");
+  if (P.arith == CEEDBP_ARITH_DF64 && !gll_quad && !((P.bp == 1 || P.bp == 3) && P.order <= 11))
+    return fail(c, CEEDBP_EUNSUPPORTED,
+                "the FP32-pair arithmetic is built for BP5 and BP6, and for BP1 and BP3 up to order 11");
   c->arith = P.arith;
   if (P.geom != CEEDBP_GEOM_STORED && P.geom != CEEDBP_GEOM_RECOMPUTE) return fail(c, CEEDBP_EINVAL, "unknown geom");
   const bool recompute = P.geom == CEEDBP_GEOM_RECOMPUTE;
@@ -210,6 +211,7 @@ ceedbp_status setup_impl(ceedbp_ctx* c, const double* coords, const int64_t* l2g
 
   int nb_apply = elem_blocks(m);
   if (c->colloc) nb_apply = std::max(nb_apply, std::max(int(P.nelem), elem_lp_blocks(m)));
+  else if (P.arith == CEEDBP_ARITH_DF64) nb_apply = std::max(nb_apply, elem_dfgl_blocks(m));
   CK(c, dalloc(&c->d_part_apply, size_t(nb_apply) * nc));
   CK(c, dalloc(&c->d_part_vec, size_t(vec_blocks(n)) * 3 * nc));
 
@@ -288,7 +290,31 @@ ceedbp_status setup_impl(ceedbp_ctx* c, const double* coords, const int64_t* l2g
       CK(c, launch_elem(m, kMass, a, s));
     }
   }
-  if (c->arith == CEEDBP_ARITH_DF64) {
+  if (c->arith == CEEDBP_ARITH_DF64 && !c->colloc) {
+    // BP1 / BP3: pair copies of the factors (G, or the mass factors), of J and Dq, and of dinv;
+    // the kernel sets its splitters from its own line data and the tables' row sums
+    const size_t ng = c->op_kind == kStiff ? size_t(P.nelem) * 6 * Q3 : size_t(P.nelem) * Q3;
+    CK(c, dalloc(&c->d_Gdf, ng));
+    CK(c, dalloc(&c->d_Ddf, size_t(qdef) * p1 + size_t(qdef) * qdef));
+    CK(c, dalloc(&c->d_dinvdf, n));
+    CK(c, launch_f64_to_df(c->op_kind == kStiff ? c->d_G : c->d_Mq, c->d_Gdf, int64_t(ng), s));
+    CK(c, launch_f64_to_df(c->d_dinv, c->d_dinvdf, n, s));
+    std::vector<dfloat> hd(size_t(qdef) * p1 + size_t(qdef) * qdef);
+    auto to_pair = [](double d) { const float hi = float(d); return dfloat{hi, float(d - double(hi))}; };
+    for (size_t i = 0; i < basis.J.size(); ++i) hd[i] = to_pair(basis.J[i]);
+    for (size_t i = 0; i < basis.Dq.size(); ++i) hd[basis.J.size() + i] = to_pair(basis.Dq[i]);
+    CK(c, cudaMemcpyAsync(c->d_Ddf, hd.data(), sizeof(dfloat) * hd.size(), cudaMemcpyHostToDevice, s));
+    CK(c, cudaStreamSynchronize(s));
+    ElemDfArgs a = {};
+    a.u_f64 = c->d_r;
+    a.wl = reinterpret_cast<dfloat*>(c->d_wl);
+    a.G = c->d_Gdf;
+    a.D = c->d_Ddf;
+    a.mask_in = 1;
+    a.fault = &c->d_state->fault;
+    CK(c, launch_elem_df(m, a, s));  // one launch outside any capture (attribute setup)
+    CK(c, cudaStreamSynchronize(s));
+  } else if (c->arith == CEEDBP_ARITH_DF64) {
     // pair copies of G, D and dinv; splitter bounds from the row and column sums of |D|
     const size_t ng = size_t(P.nelem) * 6 * Q3;
     CK(c, dalloc(&c->d_Gdf, ng));
@@ -972,7 +998,8 @@ ceedbp_status ceedbp_bk_apply(ceedbp_ctx* c, const double* uL, double* wL) {
 
 ceedbp_status ceedbp_set_tile(ceedbp_ctx* c, int eb, int schedule, int seq) {
   if (!c) return fail(c, CEEDBP_EINVAL, "null context");
-  if (c->arith != CEEDBP_ARITH_DF64) return fail(c, CEEDBP_EUNSUPPORTED, "tile shapes belong to the pair path");
+  if (c->arith != CEEDBP_ARITH_DF64 || !c->colloc)
+    return fail(c, CEEDBP_EUNSUPPORTED, "tile shapes belong to the pair path of BP5/BP6");
   int cand_eb[32], cand_st[32], cand_ns[32];
   const int ncand = elem_df_tile_candidates(c->mesh, cand_eb, cand_st, cand_ns, 32, true);
   int hit = -1;

@@ -155,6 +155,10 @@ struct ElemDfArgs;
 int elem_df_tile_candidates(const DeviceMesh& m, int* eb, int* stage, int* ns, int cap, bool pipelined);
 cudaError_t set_df_dconst(int p1, const dfloat* host, cudaStream_t s);
 cudaError_t launch_elem_df(const DeviceMesh& m, const ElemDfArgs& a, cudaStream_t s);
+// BP1/BP3 (Gauss quadrature) on FP32 pairs; a.D holds the pair tables J [q][p1] then Dq [q][q].
+bool elem_dfgl_supported(const DeviceMesh& m);
+int elem_dfgl_blocks(const DeviceMesh& m);
+cudaError_t launch_elem_dfgl(const DeviceMesh& m, const ElemDfArgs& a, cudaStream_t s);
 cudaError_t launch_init_df(const DeviceMesh& m, const double* b, const double* ax, double* x, dfloat* xd, dfloat* r,
                            dfloat* p, const dfloat* dinv, int x0, double* partials, SolveState* st, double tol,
                            int fixed, cudaStream_t s);

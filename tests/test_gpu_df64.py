@@ -1,6 +1,7 @@
 """Parity of the FP64-accurate FP32-pair path (CEEDBP_ARITH_DF64) with the
 CPU FP64 oracle, at the FP64 tolerances: one apply within 1e-12 relative, CG
-iteration counts within 1, final relative residuals within 1e-10."""
+iteration counts within 1, final relative residuals within 1e-10.  BP5/BP6
+(collocated) and BP1/BP3 (Gauss quadrature, orders 1..11)."""
 import numpy as np
 import pytest
 import torch
@@ -39,7 +40,10 @@ def _rel(a, b):
 
 @pytest.mark.parametrize("bp,N,dims", [(5, 1, (3, 2, 2)), (5, 2, (3, 3, 3)), (5, 3, (3, 2, 5)), (5, 4, (2, 3, 2)),
                                         (5, 5, (2, 2, 2)), (5, 7, (3, 2, 2)), (5, 8, (2, 1, 2)), (5, 11, (2, 1, 1)),
-                                        (5, 15, (1, 1, 1)), (6, 2, (2, 2, 2)), (6, 3, (3, 2, 2)), (6, 7, (2, 1, 1))])
+                                        (5, 15, (1, 1, 1)), (6, 2, (2, 2, 2)), (6, 3, (3, 2, 2)), (6, 7, (2, 1, 1)),
+                                        (3, 1, (3, 2, 2)), (3, 2, (2, 3, 2)), (3, 3, (3, 2, 2)), (3, 5, (2, 2, 1)),
+                                        (3, 7, (2, 1, 2)), (3, 11, (1, 1, 1)), (1, 1, (2, 2, 3)), (1, 3, (3, 2, 2)),
+                                        (1, 7, (2, 1, 1)), (1, 11, (1, 1, 1))])
 def test_df64_apply_parity(bp, N, dims):
     op = _box(bp, dims, N)
     ref = BakeoffProblem(bp, *dims, N, amp=0.05)
@@ -49,7 +53,8 @@ def test_df64_apply_parity(bp, N, dims):
     assert err < APPLY_TOL, err
 
 
-@pytest.mark.parametrize("bp,N,dims", [(5, 3, (3, 2, 2)), (5, 7, (2, 2, 2)), (6, 3, (2, 2, 2)), (5, 2, (4, 3, 3))])
+@pytest.mark.parametrize("bp,N,dims", [(5, 3, (3, 2, 2)), (5, 7, (2, 2, 2)), (6, 3, (2, 2, 2)), (5, 2, (4, 3, 3)),
+                                        (3, 3, (3, 2, 2)), (3, 7, (2, 2, 1)), (1, 5, (2, 2, 2))])
 def test_df64_solve_parity(bp, N, dims):
     op = _box(bp, dims, N)
     ref = BakeoffProblem(bp, *dims, N, amp=0.05)
@@ -172,3 +177,30 @@ def test_pipelined_schedule_solve_parity(bp, N, dims, tile):
         assert abs(info["rel_res"][c] - infos[c]["rel_res"]) <= 1e-10
     res = np.linalg.norm(ref.apply(x.cpu().numpy()) - b) / np.linalg.norm(b)
     assert res < 1e-7
+
+
+@pytest.mark.parametrize("bp,N,k", [(3, 7, 18), (1, 7, 18)])
+def test_df64_gauss_sampled_rows_at_bench_size(bp, N, k):
+    """BP3 and BP1 in pair arithmetic at the bench size (E = 2^18, N = 7) on 200+ sampled rows
+    (vertices, edges, faces and interiors of probe elements, the last element among them)."""
+    dims = box_dims(k)
+    op = _box(bp, dims, N)
+    n = op.nglobal
+    u_h = uniform_pm1(9, np.arange(n))
+    w = op.apply(torch.from_numpy(u_h).cuda())
+    nodes = probe_nodes(dims, N, seed=k + bp)
+    assert len(nodes) >= 200
+    rows = sampled_rows(bp, *dims, N, 0.05, lambda ids: u_h[ids], nodes)
+    got = w[torch.from_numpy(nodes).cuda()].cpu().numpy()
+    err = np.linalg.norm(got - rows) / np.linalg.norm(rows)
+    print(f"pair path BP{bp} N={N} E=2^{k}: {len(nodes)} rows, relative error {err:.2e}")
+    assert err <= APPLY_TOL, err
+    op.close()
+
+
+def test_df64_gauss_unsupported_cases():
+    for bp, N in ((3, 12), (4, 3), (2, 3)):
+        c, l, d = pkg.mesh_box(1, 1, 1, N, 0.05)
+        with pytest.raises(pkg.CeedbpError) as ei:
+            pkg.Operator(bp, N, c, l, d, arith=pkg.ARITH_DF64)
+        assert ei.value.status == pkg.EUNSUPPORTED
