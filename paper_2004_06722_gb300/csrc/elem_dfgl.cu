@@ -63,6 +63,28 @@ __device__ __forceinline__ void line_mul(const dfloat* M, int lda, int ldn, floa
   }
 }
 
+// The same with the outputs stored to shared memory, out[a * ostride], one output at a time
+// (a rolled loop keeps the code of the many line stages small enough for the instruction cache)
+template <int A, int B>
+__device__ __forceinline__ void line_mul_to(const dfloat* M, int lda, int ldn, float R, const dfloat (&x)[B],
+                                            dfloat* out, int ostride) {
+  float mx = 0.0f;
+#pragma unroll
+  for (int n = 0; n < B; ++n) mx = fmaxf(mx, fabsf(x[n].hi));
+  const float sig = splitter(__fmul_rn(__fmul_rn(mx, R), kBoundSlack));
+#pragma unroll 1
+  for (int a = 0; a < A; ++a) {
+    SplitAcc acc(sig);
+    const dfloat* Ma = M + a * lda;
+#pragma unroll
+    for (int n = 0; n < B; ++n) {
+      const dfloat m = Ma[n * ldn];
+      acc.add(m.hi, m.lo, x[n].hi, x[n].lo);
+    }
+    out[a * ostride] = norm_pair(acc.result(sig));
+  }
+}
+
 // (g_k0 ur + g_k1 us + g_k2 ut) with a splitter from this point's values
 __device__ __forceinline__ dfloat grow(dfloat g0, dfloat g1, dfloat g2, dfloat ur, dfloat us, dfloat ut, float mx) {
   const float rs = fabsf(g0.hi) + fabsf(g1.hi) + fabsf(g2.hi);
@@ -132,23 +154,19 @@ __global__ void __launch_bounds__(DfGlShape<P1, Q>::THREADS) elem_dfgl_kernel(co
 
   // ---- x: line (j, k) = t along i
   if (active && t < P1 * P1) {
-    dfloat x[P1], y[Q];
+    dfloat x[P1];
 #pragma unroll
     for (int i = 0; i < P1; ++i) x[i] = sU[t * P1 + i];
-    line_mul<Q, P1>(sJ, P1, 1, RJ, x, y);
-#pragma unroll
-    for (int q = 0; q < Q; ++q) sA[t * Q + q] = y[q];
+    line_mul_to<Q, P1>(sJ, P1, 1, RJ, x, sA + t * Q, 1);
   }
   __syncthreads();
   // ---- y: line (qx, k) along j
   if (active && t < Q * P1) {
     const int qx = t % Q, k = t / Q;
-    dfloat x[P1], y[Q];
+    dfloat x[P1];
 #pragma unroll
     for (int j = 0; j < P1; ++j) x[j] = sA[qx + Q * (j + P1 * k)];
-    line_mul<Q, P1>(sJ, P1, 1, RJ, x, y);
-#pragma unroll
-    for (int q = 0; q < Q; ++q) sB[qx + Q * (q + Q * k)] = y[q];
+    line_mul_to<Q, P1>(sJ, P1, 1, RJ, x, sB + qx + QQ * k, Q);
   }
   __syncthreads();
   // ---- z: column (qx, qy) = t
@@ -175,17 +193,13 @@ __global__ void __launch_bounds__(DfGlShape<P1, Q>::THREADS) elem_dfgl_kernel(co
     __syncthreads();
     if (active) {  // u_r on line (qy, z) = (lo, hi), u_s on line (qx, z) = (lo, hi)
       const int lo = t % Q, hi = t / Q;
-      dfloat x[Q], y[Q];
+      dfloat x[Q];
 #pragma unroll
       for (int n = 0; n < Q; ++n) x[n] = sC[n + Q * lo + QQ * hi];
-      line_mul<Q, Q>(sD, Q, 1, RD, x, y);
-#pragma unroll
-      for (int n = 0; n < Q; ++n) sA[n + Q * lo + QQ * hi] = y[n];
+      line_mul_to<Q, Q>(sD, Q, 1, RD, x, sA + Q * lo + QQ * hi, 1);
 #pragma unroll
       for (int n = 0; n < Q; ++n) x[n] = sC[lo + Q * n + QQ * hi];
-      line_mul<Q, Q>(sD, Q, 1, RD, x, y);
-#pragma unroll
-      for (int n = 0; n < Q; ++n) sB[lo + Q * n + QQ * hi] = y[n];
+      line_mul_to<Q, Q>(sD, Q, 1, RD, x, sB + lo + QQ * hi, Q);
     }
     __syncthreads();
     dfloat wt[Q];
@@ -208,17 +222,13 @@ __global__ void __launch_bounds__(DfGlShape<P1, Q>::THREADS) elem_dfgl_kernel(co
     __syncthreads();
     if (active) {  // transposes Dq^T (row a of Dq^T is column a of Dq), r and s in place
       const int lo = t % Q, hi = t / Q;
-      dfloat x[Q], y[Q];
+      dfloat x[Q];
 #pragma unroll
       for (int n = 0; n < Q; ++n) x[n] = sA[n + Q * lo + QQ * hi];
-      line_mul<Q, Q>(sD, 1, Q, RDT, x, y);
-#pragma unroll
-      for (int n = 0; n < Q; ++n) sA[n + Q * lo + QQ * hi] = y[n];
+      line_mul_to<Q, Q>(sD, 1, Q, RDT, x, sA + Q * lo + QQ * hi, 1);
 #pragma unroll
       for (int n = 0; n < Q; ++n) x[n] = sB[lo + Q * n + QQ * hi];
-      line_mul<Q, Q>(sD, 1, Q, RDT, x, y);
-#pragma unroll
-      for (int n = 0; n < Q; ++n) sB[lo + Q * n + QQ * hi] = y[n];
+      line_mul_to<Q, Q>(sD, 1, Q, RDT, x, sB + lo + QQ * hi, Q);
       line_mul<Q, Q>(sD, 1, Q, RDT, wt, vq);
     }
     __syncthreads();
@@ -239,22 +249,18 @@ __global__ void __launch_bounds__(DfGlShape<P1, Q>::THREADS) elem_dfgl_kernel(co
   // ---- y^T: line (qx, k)
   if (active && t < Q * P1) {
     const int qx = t % Q, k = t / Q;
-    dfloat x[Q], y[P1];
+    dfloat x[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) x[q] = sC[qx + Q * (q + Q * k)];
-    line_mul<P1, Q>(sJ, 1, P1, RJT, x, y);
-#pragma unroll
-    for (int j = 0; j < P1; ++j) sA[qx + Q * (j + P1 * k)] = y[j];
+    line_mul_to<P1, Q>(sJ, 1, P1, RJT, x, sA + qx + Q * P1 * k, Q);
   }
   __syncthreads();
   // ---- x^T: line (j, k) = t
   if (active && t < P1 * P1) {
-    dfloat x[Q], y[P1];
+    dfloat x[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) x[q] = sA[q + Q * t];
-    line_mul<P1, Q>(sJ, 1, P1, RJT, x, y);
-#pragma unroll
-    for (int i = 0; i < P1; ++i) sB[t * P1 + i] = y[i];
+    line_mul_to<P1, Q>(sJ, 1, P1, RJT, x, sB + t * P1, 1);
   }
   __syncthreads();
   dfloat acc_dot{0.0f, 0.0f};
@@ -294,7 +300,11 @@ cudaError_t launch_dfgl_t(const DeviceMesh& m, const ElemDfArgs& a, cudaStream_t
   using S = DfGlShape<P1, Q>;
   const size_t smem = sizeof(double) * 32 + sizeof(float) * 4 + sizeof(dfloat) * (S::TAB + size_t(S::EB) * S::SLOT);
   auto kern = elem_dfgl_kernel<P1, Q, KIND>;
-  static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  static const cudaError_t attr = [&] {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    return e;
+  }();
   if (attr != cudaSuccess) return attr;
   const int64_t blocks = (m.nelem + S::EB - 1) / S::EB;
   kern<<<unsigned(blocks), S::THREADS, smem, s>>>(m, a);
