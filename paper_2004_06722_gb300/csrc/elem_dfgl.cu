@@ -149,6 +149,15 @@ __global__ void __launch_bounds__(DfGlShape<P1, Q>::THREADS) elem_dfgl_kernel(co
       sU[idx] = v;
     }
   }
+  // BK1: the column's mass factors are loaded now, their latency hidden behind the x and y stages
+  dfloat mq[KIND == kMass ? Q : 1];
+  if constexpr (KIND == kMass) {
+    if (active) {
+      const dfloat* M = a.G + e * Q3;
+#pragma unroll
+      for (int z = 0; z < Q; ++z) mq[z] = M[t + QQ * z];
+    }
+  }
   __syncthreads();
   const float RJ = rows[0], RJT = rows[1], RD = rows[2], RDT = rows[3];
 
@@ -185,9 +194,8 @@ __global__ void __launch_bounds__(DfGlShape<P1, Q>::THREADS) elem_dfgl_kernel(co
   dfloat vq[Q];
   if constexpr (KIND == kMass) {
     if (active) {
-      const dfloat* M = a.G + e * Q3;
 #pragma unroll
-      for (int z = 0; z < Q; ++z) vq[z] = norm_pair(dw_mul(M[t + QQ * z], uq[z]));
+      for (int z = 0; z < Q; ++z) vq[z] = norm_pair(dw_mul(mq[z], uq[z]));
     }
   } else {
     __syncthreads();

@@ -105,3 +105,52 @@ def test_gradient_matches_central_differences_and_autograd():
         fd = (Jof(k0 + h * d) - Jof(k0 - h * d)) / (2 * h)
         ad = float((g * d).sum())
         assert abs(fd - ad) <= 1e-6 * abs(ad), (fd, ad)
+
+
+def test_central_differences_at_16_cubed_both_measures():
+    """E = 16^3, N = 7 (1.4e6 DOFs, 2.1e6 kappa values), the benchmark's adjoint workload at a
+    reduced size: forcing f = 1, kappa = exp(g) from 16 Fourier modes, 20 random directions
+    (entries U[-1, 1], max 1) and 5 smooth ones (log-kappa Fourier perturbations).  Central
+    differences with h = 1e-6 and solves to 1e-13 against <grad J, d>: the plain relative
+    error within the 1e-6 bar on every direction, and the error in the scale of the direction,
+    |fd - <g,d>| / sum |g_i d_i|, within 1e-9."""
+    E1, N = 16, 7
+    coords, l2g, dirichlet = pkg.mesh_box(E1, E1, E1, N, 0.05)
+    kappa = torch.from_numpy(np.exp(fourier_field(fourier_modes(0), coords))).cuda()
+    kappa_star = torch.from_numpy(np.exp(fourier_field(fourier_modes(1), coords))).cuda()
+    op = pkg.Operator(5, N, coords, l2g, dirichlet)
+    mask = torch.from_numpy(1.0 - dirichlet.astype(np.float64)).cuda()
+    b = op.mass(torch.ones(op.nglobal, dtype=torch.float64, device="cuda")) * mask
+    op.set_kappa(kappa_star)
+    u_star, _ = op.solve(b, tol=1e-13, chunk=64)
+    u_star = u_star.clone()
+    k = kappa.clone().requires_grad_(True)
+    (g,) = torch.autograd.grad(pkg.kappa_misfit(k, op, b, u_star, tol=1e-13), k)
+
+    def Jof(kap):
+        op.set_kappa(kap)
+        u, _ = op.solve(b, tol=1e-13, chunk=64)
+        return op.misfit(u, u_star)[1]
+
+    h = 1e-6
+    rng = np.random.default_rng(20)
+    plain, scaled, smooth = [], [], []
+    for _ in range(20):
+        d = torch.from_numpy(rng.uniform(-1, 1, size=tuple(kappa.shape))).cuda()
+        d /= d.abs().max()
+        fd = (Jof(kappa + h * d) - Jof(kappa - h * d)) / (2 * h)
+        ad = float((g * d).sum())
+        plain.append(abs(fd - ad) / abs(ad))
+        scaled.append(abs(fd - ad) / float((g * d).abs().sum()))
+    for sd in range(100, 105):
+        d = torch.from_numpy(fourier_field(fourier_modes(sd), coords)).cuda()
+        d /= d.abs().max()
+        fd = (Jof(kappa + h * d * kappa) - Jof(kappa - h * d * kappa)) / (2 * h)
+        ad = float((g * d * kappa).sum())
+        smooth.append(abs(fd - ad) / abs(ad))
+    print(f"E=16^3 FD: plain max {max(plain):.2e} median {np.median(plain):.2e}, scaled max {max(scaled):.2e}, "
+          f"smooth max {max(smooth):.2e}")
+    assert max(plain) <= 1e-6
+    assert max(scaled) <= 1e-9
+    assert max(smooth) <= 1e-6
+    op.close()

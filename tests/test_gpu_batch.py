@@ -24,8 +24,8 @@ def _need_gpu():
     pkg.load_library()
 
 
-def _problems(n, k_max, arith=pkg.ARITH_DF64, seed=3):
-    draws = batched_problems(n_problems=n, seed=seed, k_max=k_max)
+def _problems(n, k_max, arith=pkg.ARITH_DF64, seed=3, orders=(3, 5, 7)):
+    draws = batched_problems(n_problems=n, seed=seed, k_max=k_max, orders=orders)
     probs, rhs, meshes = [], [], []
     for q in draws:
         coords, l2g, dirichlet = pkg.mesh_box(q["k"], q["k"], q["k"], q["N"], q["amp"])
@@ -117,4 +117,26 @@ def test_batch_largest_member_on_sampled_rows(arith):
     print(f"batch arith={arith}: largest member k={q['k']} N={q['N']}: sampled residual {res:.2e}")
     assert infos[big]["status"] == "OK"
     assert res <= 1e-9, res
+    batch.close()
+
+
+@pytest.mark.parametrize("arith", [pkg.ARITH_FP64, pkg.ARITH_DF64])
+def test_batch_even_orders(arith):
+    """Even orders (2, 4, 6: the column kernel in FP64, the pair kernel's other shapes) batched:
+    every member within one iteration of its single solve, two members against the oracle."""
+    draws, probs, rhs = _problems(10, 4, arith, seed=7, orders=(2, 4, 6))
+    assert {q["N"] for q in draws} == {2, 4, 6}
+    batch = pkg.Batch(probs, arith=arith)
+    xs, infos = batch.solve([b for b, _ in rhs], tol=1e-10)
+    for k, (b, op) in enumerate(rhs):
+        x1, i1 = op.solve(b, tol=1e-10)
+        assert infos[k]["status"] == "OK" and infos[k]["rel_res"][0] <= 1e-10
+        assert abs(infos[k]["iters"][0] - i1["iters"][0]) <= 1
+    for k in range(2):
+        q = draws[k]
+        ref = BakeoffProblem(5, q["k"], q["k"], q["k"], q["N"], amp=q["amp"])
+        bh = ref.rhs(uniform_pm1(q["rhs_seed"], np.arange(ref.n_global)))
+        xr, ir = ref.solve(bh, tol=1e-10)
+        assert abs(infos[k]["iters"][0] - ir[0]["iters"]) <= 1
+        assert np.linalg.norm(xs[k].cpu().numpy() - xr) <= 1e-8 * np.linalg.norm(xr)
     batch.close()
