@@ -1,5 +1,9 @@
-// Element operator kernels (BK1, BK3, BK5, BK6): w^e = A^e u^e or B^e u^e for
-// every element, the unassembled product A_L Q u of Eq. (21).
+// Element operator kernels (the column kernel): w^e = A^e u^e or B^e u^e for
+// every element, the unassembled product A_L Q u of Eq. (21).  It serves BK5/BK6
+// at even orders, BK2/BK4, and BK3 at order 14; BK1/BK3 otherwise run the
+// even-odd kernel of elem_gl.cuh, and BK5/BK6 at odd orders that of elem_eo.cuh.
+// The even-odd tables and products (EoTab, eo_build, eo_mul) defined here are
+// shared by those kernels.
 //
 // Stiffness, Eq. (22): w^e = sum_{m,m'} D_m^T G_mm' D_m' u^e with the
 // geometric factors G of Eq. (23) (six symmetric components per quadrature
