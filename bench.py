@@ -69,7 +69,9 @@ def parse_args():
                     help="skip the compact runs of the other configurations (BP1/BP3 points, BP6 defect "
                          "correction, batched solves, adjoint gradient)")
     ap.add_argument("--cpu-sample-k", type=int, default=9, help="E = 2^k elements for the oracle sample")
-    ap.add_argument("--workload", choices=["sweep", "batched", "mixed", "adjoint", "bp-sweep", "bk-sweep", "bp-point"], default="sweep",
+    ap.add_argument("--cpu-max-k", type=int, default=13, help="largest E = 2^k of the cpu-sweep workload")
+    ap.add_argument("--workload", choices=["sweep", "batched", "mixed", "adjoint", "bp-sweep", "bk-sweep", "bp-point",
+                                           "cpu-sweep"], default="sweep",
                     help="sweep: BP5 n-sweep headline; batched: 256 BP5 problems batched vs one at a time; "
                          "mixed: BP6 defect correction vs FP64 PCG; adjoint: dJ/dkappa pipeline")
     return ap.parse_args()
@@ -449,6 +451,13 @@ def cpu_model() -> str:
                     return line.split(":", 1)[1].strip()
     except OSError:
         pass
+    try:  # Arm hosts name the core in lscpu only
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
     import platform
     return platform.processor() or platform.machine()
 
@@ -484,6 +493,85 @@ def cpu_baseline(N, k, iters):
                       f"iterations of the oracle on the assembled CSR matrix, rows split over {threads} POSIX "
                       f"threads; assembly by naive full quadrature {t_setup:.1f} s excluded",
             "host_cpus": os.cpu_count(), "cpu_model": cpu_model()}
+
+
+def _assemble_chunk(task):
+    """Element matrices of one range of elements by the oracle (naive full quadrature) and their
+    assembled sum over that range (the oracle's own assembly); a worker of cpu_sweep's pool."""
+    import numpy as np
+
+    from oracle.assemble import assemble
+    from oracle.element import element_matrices
+    from oracle.mesh import box_mesh, global_count
+    from oracle.quadrature import bp_rule
+    dims, N, e0, e1 = task
+    coords, l2g = box_mesh(*dims, N, 0.05, elements=np.arange(e0, e1))
+    rule = bp_rule(5, N)
+    mats = [element_matrices(coords[e], N, rule, want=("A",))["A"] for e in range(e1 - e0)]
+    A = assemble(l2g, mats, global_count(*dims, N)).tocoo()
+    return A.row.astype(np.int32), A.col.astype(np.int32), A.data
+
+
+def run_cpu_sweep(args):
+    """The oracle's PCG rate on all host cores against the problem size: BP5 at order --order on
+    E = 2^k for k = 9 .. --cpu-max-k, assembled by the oracle's element matrices on a process pool
+    (spawn; assembly not timed), 20 PCG iterations of the oracle's C PCG on POSIX threads."""
+    import multiprocessing as mp
+
+    import numpy as np
+    import scipy.sparse as sp
+
+    from oracle.assemble import restrict
+    from oracle.cpu_pcg import host_threads, pcg_threads
+    from oracle.mesh import boundary_nodes, global_count
+    from synth import box_dims, uniform_pm1
+    N = args.order
+    threads = host_threads()
+    out = []
+    # one BLAS thread per worker process (the pool already uses every core)
+    saved = {v: os.environ.get(v) for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for v in saved:
+        os.environ[v] = "1"
+    pool = mp.get_context("spawn").Pool(threads)
+    for v, old in saved.items():
+        if old is None:
+            os.environ.pop(v, None)
+        else:
+            os.environ[v] = old
+    with pool:
+        for k in range(9, args.cpu_max_k + 1):
+            dims = box_dims(k)
+            E = dims[0] * dims[1] * dims[2]
+            ng = global_count(*dims, N)
+            t0 = time.perf_counter()
+            step = 32
+            parts = pool.map(_assemble_chunk, [(dims, N, e, min(E, e + step)) for e in range(0, E, step)])
+            rows = np.concatenate([p[0] for p in parts])
+            cols = np.concatenate([p[1] for p in parts])
+            vals = np.concatenate([p[2] for p in parts])
+            del parts
+            A = sp.csr_matrix((vals, (rows, cols)), shape=(ng, ng))
+            del rows, cols, vals
+            A.sum_duplicates()
+            free = ~boundary_nodes(*dims, N)
+            A_free = restrict(A, free)
+            del A
+            t_asm = time.perf_counter() - t0
+            b = uniform_pm1(0, np.arange(ng))[free]
+            pcg_threads(A_free, b, A_free.diagonal(), 2, threads)
+            t0 = time.perf_counter()
+            pcg_threads(A_free, b, A_free.diagonal(), 20, threads)
+            t = time.perf_counter() - t0
+            n = E * N ** 3
+            row = {"k": k, "elements": list(dims), "n": n, "nnz": int(A_free.nnz),
+                   "csr_gb": (A_free.nnz * 12 + A_free.shape[0] * 8) / 1e9, "assembly_s": t_asm,
+                   "dofs_per_s": n * 20 / t, "ms_per_iter": t / 20 * 1e3}
+            out.append(row)
+            print(json.dumps(row), file=sys.stderr, flush=True)
+            del A_free
+    print(json.dumps({"metric": "oracle PCG DOFs/s per iteration on all host cores vs n (BP5)", "unit": "DOFs/s",
+                      "order": N, "threads": threads, "cpu_model": cpu_model(), "host_cpus": os.cpu_count(),
+                      "results": out}), flush=True)
 
 
 def run_reference(args):
@@ -890,6 +978,8 @@ def main():
         return run_mixed(args)
     if args.workload == "adjoint":
         return run_adjoint(args)
+    if args.workload == "cpu-sweep":
+        return run_cpu_sweep(args)
     if args.impl == "reference":
         run_reference(args)
     else:
