@@ -60,6 +60,7 @@ def parse_args():
     ap.add_argument("--mixed-bp", type=int, default=6, choices=[5, 6], help="bake-off problem of the mixed workload")
     ap.add_argument("--bp", type=int, default=3, help="bake-off problem of the bp-point workload")
     ap.add_argument("--bps", default="1,3,5", help="bake-off problems of the bp-sweep workload")
+    ap.add_argument("--bk-bps", default="", help="element operators of the bk-sweep workload (default: 5)")
     ap.add_argument("--df-tile", default=None,
                     help="pin the pair kernel's shape 'eb,schedule,seq' instead of the autotuner's choice")
     ap.add_argument("--geom", choices=["stored", "recompute"], default="stored",
@@ -834,61 +835,81 @@ def run_bp_sweep(args):
                       "unit": "DOFs/s", "iters": iters, "results": out}), flush=True)
 
 
+def bk_flops(bp: int, N: int) -> int:
+    """Algorithmic flops of one element of BK`bp` (per component): BK5/BK6 12 p1^4 + 15 p1^3 (Eq. (22)
+    with J = I); BK3/BK4 the interpolate-then-differentiate count 4 p1^4 (3 g^4 + g^3 + g^2 + g) +
+    15 g^3 p1^3 with g = q / p1 (Eqs. (31)-(33)); BK1/BK2 the mass J^T B J, 4 p1^4 (g + g^2 + g^3) + g^3 p1^3
+    (Eq. (34))."""
+    p1 = N + 1
+    if bp in (5, 6):
+        return 12 * p1 ** 4 + 15 * p1 ** 3
+    g = (N + 2) / p1
+    if bp in (3, 4):
+        return int(round(4 * p1 ** 4 * (3 * g ** 4 + g ** 3 + g ** 2 + g) + 15 * g ** 3 * p1 ** 3))
+    return int(round(4 * p1 ** 4 * (g + g ** 2 + g ** 3) + g ** 3 * p1 ** 3))
+
+
 def run_bk_sweep(args):
-    """Unassembled BK5 (BP5 element operator, no Q, Q^T or mask; ceedbp_bk_apply) at N in {1, 2, 3, 5, 7,
-    9, 11, 15}, FP64 and FP32 pairs, on E = 2^k boxes (k <= 21) with n = E N^3 from ~1e3 to ~1e8 (k in steps of 2):
-    time per apply (CUDA events over `--sweep-iters` applies after 3 warm-ups), algorithmic GFLOP/s
-    (12 p1^4 + 15 p1^3 per element), DOFs/s and r_max, n_0.8 per (arith, N)."""
+    """Unassembled BK kernels (the element operators of the BPs in --bps, no Q, Q^T or mask;
+    ceedbp_bk_apply) at N in {1, 2, 3, 5, 7, 9, 11, 15}, FP64 and FP32 pairs (where built), on E = 2^k boxes
+    (k <= 21) with n = E N^3 from ~1e3 to ~1e8 (k in steps of 2): time per apply (CUDA events over
+    `--sweep-iters` applies after 3 warm-ups), algorithmic GFLOP/s (bk_flops per element), DOFs/s and r_max,
+    n_0.8 per (BK, arith, N).  The default runs BK5; --bk-bps 1,3,5 adds BK1 and BK3."""
     import numpy as np
     import torch
 
     import paper_2004_06722_gb300 as pkg
     from synth import box_dims, uniform_pm1
     reps = args.sweep_iters
+    bps = [int(v) for v in (args.bk_bps or "5").split(",")]
     out = {}
-    for name, arith in (("fp64", pkg.ARITH_FP64), ("df64", pkg.ARITH_DF64)):
-        for N in (1, 2, 3, 5, 7, 9, 11, 15):
-            p1 = N + 1
-            ns, rates, gflops, tpp = [], [], [], []
-            k = 0
-            while 2 ** k * N ** 3 < 1e3:
-                k += 1
-            while 2 ** k * N ** 3 <= 1.2e8 and k <= 21:
-                dims = box_dims(k)
-                E = dims[0] * dims[1] * dims[2]
-                coords, l2g, dirichlet = pkg.mesh_box(*dims, N, 0.05)
-                op = pkg.Operator(5, N, coords, l2g, dirichlet, arith=arith)
-                del coords, l2g
-                uL = torch.from_numpy(uniform_pm1(0, np.arange(E * p1 ** 3)).reshape(E, p1 ** 3)).cuda()
-                wL = torch.empty_like(uL)
-                for _ in range(3):
-                    op.bk_apply(uL, wL)
-                ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                with torch.cuda.stream(op.stream):
-                    torch.cuda.synchronize()
-                    ev0.record(op.stream)
-                    for _ in range(reps):
+    for bp in bps:
+        for name, arith in (("fp64", pkg.ARITH_FP64), ("df64", pkg.ARITH_DF64)):
+            for N in (1, 2, 3, 5, 7, 9, 11, 15):
+                if arith == pkg.ARITH_DF64 and bp in (1, 3) and N > 11:
+                    continue  # the pair path of BK1/BK3 is built up to order 11
+                p1 = N + 1
+                ns, rates, gflops, tpp = [], [], [], []
+                k = 0
+                while 2 ** k * N ** 3 < 1e3:
+                    k += 1
+                while 2 ** k * N ** 3 <= 1.2e8 and k <= 21:
+                    dims = box_dims(k)
+                    E = dims[0] * dims[1] * dims[2]
+                    coords, l2g, dirichlet = pkg.mesh_box(*dims, N, 0.05)
+                    op = pkg.Operator(bp, N, coords, l2g, dirichlet, arith=arith)
+                    del coords, l2g
+                    uL = torch.from_numpy(uniform_pm1(0, np.arange(E * p1 ** 3)).reshape(E, p1 ** 3)).cuda()
+                    wL = torch.empty_like(uL)
+                    for _ in range(3):
                         op.bk_apply(uL, wL)
-                    ev1.record(op.stream)
-                torch.cuda.synchronize()
-                t = ev0.elapsed_time(ev1) * 1e-3 / reps
-                n = E * N ** 3
-                ns.append(n)
-                rates.append(n / t)
-                gflops.append(E * (12 * p1 ** 4 + 15 * p1 ** 3) / t / 1e9)
-                tpp.append(t / n)
-                op.close()
-                del uL, wL
-                torch.cuda.empty_cache()
-                k += 2
-            rmax = max(rates)
-            n80 = n_08(ns, rates)
-            out[f"{name}_N{N}"] = {"n": ns, "dofs_per_s": rates, "gflops": gflops, "s_per_dof": tpp,
-                                   "r_max": rmax, "n_0.8": n80, "gflops_max": max(gflops)}
-            print(json.dumps({f"{name}_N{N}": {"r_max": rmax, "n_0.8": n80, "gflops_max": max(gflops)}}),
-                  file=sys.stderr, flush=True)
-    print(json.dumps({"metric": "unassembled BK5 apply: DOFs/s and GFLOP/s vs n (FP64 and FP32 pairs)",
-                      "unit": "DOFs/s", "reps": reps, "results": out}), flush=True)
+                    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    with torch.cuda.stream(op.stream):
+                        torch.cuda.synchronize()
+                        ev0.record(op.stream)
+                        for _ in range(reps):
+                            op.bk_apply(uL, wL)
+                        ev1.record(op.stream)
+                    torch.cuda.synchronize()
+                    t = ev0.elapsed_time(ev1) * 1e-3 / reps
+                    n = E * N ** 3
+                    ns.append(n)
+                    rates.append(n / t)
+                    gflops.append(E * bk_flops(bp, N) / t / 1e9)
+                    tpp.append(t / n)
+                    op.close()
+                    del uL, wL
+                    torch.cuda.empty_cache()
+                    k += 2
+                rmax = max(rates)
+                n80 = n_08(ns, rates)
+                key = f"BK{bp}_{name}_N{N}"
+                out[key] = {"n": ns, "dofs_per_s": rates, "gflops": gflops, "s_per_dof": tpp,
+                            "r_max": rmax, "n_0.8": n80, "gflops_max": max(gflops)}
+                print(json.dumps({key: {"r_max": rmax, "n_0.8": n80, "gflops_max": max(gflops)}}),
+                      file=sys.stderr, flush=True)
+    print(json.dumps({"metric": "unassembled BK apply: DOFs/s and GFLOP/s vs n (FP64 and FP32 pairs)",
+                      "unit": "DOFs/s", "reps": reps, "bks": bps, "results": out}), flush=True)
 
 
 def bp_point_summary(bp, N, k, K, warmup=3, arith_name="fp64"):

@@ -76,3 +76,14 @@ def test_ncu_value_reads_instruction_counts(tmp_path, monkeypatch):
     assert bench.ncu_value("x.md", "dadd_per_element") == 3500.0
     assert bench.ncu_value("x.md", "other") is None
     assert bench.ncu_value("missing.md", "dfma_per_element") is None
+
+
+def test_bk_flop_counts_per_dof():
+    """Work per DOF of the element operators: BK5 12 p1^4 + 15 p1^3 per element (Eq. (22)),
+    BK3 the interpolate-then-differentiate count of Eqs. (31)-(33), BK1 the mass J^T B J (Eq. (34));
+    N = 7 gives 165.7, 443.6 and 184.3 flops per DOF."""
+    per_dof = {bp: bench.bk_flops(bp, 7) / 7 ** 3 for bp in (1, 3, 5)}
+    assert abs(per_dof[5] - 165.7) < 0.05
+    assert abs(per_dof[3] - 443.6) < 0.05
+    assert abs(per_dof[1] - 184.3) < 0.05
+    assert bench.bk_flops(6, 7) == bench.bk_flops(5, 7) and bench.bk_flops(4, 3) == bench.bk_flops(3, 3)
