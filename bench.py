@@ -529,47 +529,52 @@ def run_cpu_sweep(args):
     N = args.order
     threads = host_threads()
     out = []
-    # one BLAS thread per worker process (the pool already uses every core)
-    saved = {v: os.environ.get(v) for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
-    for v in saved:
-        os.environ[v] = "1"
-    pool = mp.get_context("spawn").Pool(threads)
-    for v, old in saved.items():
-        if old is None:
-            os.environ.pop(v, None)
-        else:
-            os.environ[v] = old
-    with pool:
-        for k in range(9, args.cpu_max_k + 1):
-            dims = box_dims(k)
-            E = dims[0] * dims[1] * dims[2]
-            ng = global_count(*dims, N)
-            t0 = time.perf_counter()
-            step = 32
+
+    def make_pool():
+        # one BLAS thread per worker process (the pool already uses every core)
+        saved = {v: os.environ.get(v) for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        for v in saved:
+            os.environ[v] = "1"
+        pool = mp.get_context("spawn").Pool(threads)
+        for v, old in saved.items():
+            if old is None:
+                os.environ.pop(v, None)
+            else:
+                os.environ[v] = old
+        return pool
+
+    for k in range(9, args.cpu_max_k + 1):
+        dims = box_dims(k)
+        E = dims[0] * dims[1] * dims[2]
+        ng = global_count(*dims, N)
+        t0 = time.perf_counter()
+        step = 32
+        # a pool per size, ended before the timed PCG so that no worker shares the cores
+        with make_pool() as pool:
             parts = pool.map(_assemble_chunk, [(dims, N, e, min(E, e + step)) for e in range(0, E, step)])
-            rows = np.concatenate([p[0] for p in parts])
-            cols = np.concatenate([p[1] for p in parts])
-            vals = np.concatenate([p[2] for p in parts])
-            del parts
-            A = sp.csr_matrix((vals, (rows, cols)), shape=(ng, ng))
-            del rows, cols, vals
-            A.sum_duplicates()
-            free = ~boundary_nodes(*dims, N)
-            A_free = restrict(A, free)
-            del A
-            t_asm = time.perf_counter() - t0
-            b = uniform_pm1(0, np.arange(ng))[free]
-            pcg_threads(A_free, b, A_free.diagonal(), 2, threads)
-            t0 = time.perf_counter()
-            pcg_threads(A_free, b, A_free.diagonal(), 20, threads)
-            t = time.perf_counter() - t0
-            n = E * N ** 3
-            row = {"k": k, "elements": list(dims), "n": n, "nnz": int(A_free.nnz),
-                   "csr_gb": (A_free.nnz * 12 + A_free.shape[0] * 8) / 1e9, "assembly_s": t_asm,
-                   "dofs_per_s": n * 20 / t, "ms_per_iter": t / 20 * 1e3}
-            out.append(row)
-            print(json.dumps(row), file=sys.stderr, flush=True)
-            del A_free
+        rows = np.concatenate([p[0] for p in parts])
+        cols = np.concatenate([p[1] for p in parts])
+        vals = np.concatenate([p[2] for p in parts])
+        del parts
+        A = sp.csr_matrix((vals, (rows, cols)), shape=(ng, ng))
+        del rows, cols, vals
+        A.sum_duplicates()
+        free = ~boundary_nodes(*dims, N)
+        A_free = restrict(A, free)
+        del A
+        t_asm = time.perf_counter() - t0
+        b = uniform_pm1(0, np.arange(ng))[free]
+        pcg_threads(A_free, b, A_free.diagonal(), 2, threads)
+        t0 = time.perf_counter()
+        pcg_threads(A_free, b, A_free.diagonal(), 20, threads)
+        t = time.perf_counter() - t0
+        n = E * N ** 3
+        row = {"k": k, "elements": list(dims), "n": n, "nnz": int(A_free.nnz),
+               "csr_gb": (A_free.nnz * 12 + A_free.shape[0] * 8) / 1e9, "assembly_s": t_asm,
+               "dofs_per_s": n * 20 / t, "ms_per_iter": t / 20 * 1e3}
+        out.append(row)
+        print(json.dumps(row), file=sys.stderr, flush=True)
+        del A_free
     print(json.dumps({"metric": "oracle PCG DOFs/s per iteration on all host cores vs n (BP5)", "unit": "DOFs/s",
                       "order": N, "threads": threads, "cpu_model": cpu_model(), "host_cpus": os.cpu_count(),
                       "results": out}), flush=True)
