@@ -404,7 +404,7 @@ def run_ours(args):
     if not args.no_extras and rank == 0 and world == 1:
         line["configs"] = config_summaries()
     if not args.no_cpu_baseline and rank == 0 and world == 1:
-        line["cpu_baseline"] = cpu_baseline(N, args.cpu_sample_k, iters=100)
+        line["cpu_baseline"] = cpu_baseline(N, args.cpu_sample_k)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -477,17 +477,28 @@ def oracle_sample(N, k):
     return dims, prob, b, t_setup
 
 
-def cpu_baseline(N, k, iters):
+def timed_cpu_pcg(pcg_threads, A, b, diag, threads, min_warm_s=0.5, min_timed_s=1.0):
+    """(iterations, seconds) of the oracle's threaded PCG after a warm-up of at least min_warm_s (the
+    host cores reach their clock under sustained load), timing at least min_timed_s."""
+    t0 = time.perf_counter()
+    pcg_threads(A, b, diag, 5, threads)
+    per_it = (time.perf_counter() - t0) / 5
+    pcg_threads(A, b, diag, max(5, int(math.ceil(min_warm_s / per_it))), threads)
+    iters = max(10, int(math.ceil(min_timed_s / per_it)))
+    t0 = time.perf_counter()
+    pcg_threads(A, b, diag, iters, threads)
+    return iters, time.perf_counter() - t0
+
+
+def cpu_baseline(N, k):
     """The oracle as it stands (assembled CSR, textbook Jacobi PCG) on a bounded sample: BP5 at the
     same order on E = 2^k elements, the PCG on every host core (the oracle's C PCG on POSIX threads,
-    same arithmetic as oracle/pcg.py); rate = E N^3 x iterations / PCG seconds (assembly excluded)."""
+    same arithmetic as oracle/pcg.py) for at least a second after a warm-up; rate = E N^3 x
+    iterations / PCG seconds (assembly excluded)."""
     from oracle.cpu_pcg import host_threads, pcg_threads
     dims, prob, b, t_setup = oracle_sample(N, k)
     threads = host_threads()
-    pcg_threads(prob.A_free, b, prob.diag_free, 3, threads)
-    t0 = time.perf_counter()
-    pcg_threads(prob.A_free, b, prob.diag_free, iters, threads)
-    t = time.perf_counter() - t0
+    iters, t = timed_cpu_pcg(pcg_threads, prob.A_free, b, prob.diag_free, threads)
     n = dims[0] * dims[1] * dims[2] * N ** 3
     return {"value": n * iters / t, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"BP5 N={N}, E={dims[0]}x{dims[1]}x{dims[2]} (n={n}, CSR nnz={prob.A_free.nnz}), {iters} PCG "
@@ -564,14 +575,12 @@ def run_cpu_sweep(args):
         del A
         t_asm = time.perf_counter() - t0
         b = uniform_pm1(0, np.arange(ng))[free]
-        pcg_threads(A_free, b, A_free.diagonal(), 2, threads)
-        t0 = time.perf_counter()
-        pcg_threads(A_free, b, A_free.diagonal(), 20, threads)
-        t = time.perf_counter() - t0
+        diag = A_free.diagonal()
+        iters, t = timed_cpu_pcg(pcg_threads, A_free, b, diag, threads)
         n = E * N ** 3
         row = {"k": k, "elements": list(dims), "n": n, "nnz": int(A_free.nnz),
                "csr_gb": (A_free.nnz * 12 + A_free.shape[0] * 8) / 1e9, "assembly_s": t_asm,
-               "dofs_per_s": n * 20 / t, "ms_per_iter": t / 20 * 1e3}
+               "dofs_per_s": n * iters / t, "ms_per_iter": t / iters * 1e3, "iters": iters}
         out.append(row)
         print(json.dumps(row), file=sys.stderr, flush=True)
         del A_free

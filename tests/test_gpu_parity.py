@@ -212,3 +212,22 @@ def test_sampled_rows_at_largest_sweep_size(bp, N, k, sample):
         on_boundary = rows == 0.0
         assert np.all(got[on_boundary] == 0.0)
     op.close()
+
+
+@pytest.mark.parametrize("arith", [pkg.ARITH_FP64, pkg.ARITH_DF64])
+def test_bp6_sampled_rows_at_defect_correction_size(arith):
+    """BP6 (three components sharing G) at the defect-correction configuration's size, E = 48^3,
+    N = 7 (3.8e7 DOFs per component), in both arithmetics, on 200+ sampled nodes x 3 components."""
+    dims, N = (48, 48, 48), 7
+    op = pkg.Operator.box(6, *dims, N, amp=0.05, arith=arith)
+    n = op.nglobal
+    u_h = uniform_pm1(13, np.arange(n * 3)).reshape(n, 3)
+    w = op.apply(torch.from_numpy(u_h).cuda())
+    nodes = probe_nodes(dims, N, seed=48)
+    assert len(nodes) >= 200
+    rows = sampled_rows(6, *dims, N, 0.05, lambda ids: u_h[ids], nodes)
+    got = w[torch.from_numpy(nodes).cuda()].cpu().numpy()
+    err = _rel(got, rows)
+    print(f"BP6 N=7 E=48^3 arith={arith}: {len(nodes)} nodes x 3, relative error {err:.2e}")
+    assert err <= APPLY_TOL, err
+    op.close()
