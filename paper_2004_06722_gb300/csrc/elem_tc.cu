@@ -264,8 +264,6 @@ cudaError_t launch_elem_tc_t(const DeviceMesh& m, const ElemLpArgs& a, cudaStrea
 
 bool elem_tc_supported(const DeviceMesh& m) { return m.colloc && m.p1 == kTcP1 && m.X == nullptr; }
 
-int elem_tc_blocks(const DeviceMesh& m) { return int((m.nelem + kTcWarps - 1) / kTcWarps); }
-
 cudaError_t launch_elem_tc(const DeviceMesh& m, const ElemLpArgs& a, cudaStream_t s) {
   if (!elem_tc_supported(m)) return cudaErrorInvalidValue;
   return m.ncomp == 3 ? launch_elem_tc_t<3>(m, a, s) : launch_elem_tc_t<1>(m, a, s);

@@ -184,7 +184,6 @@ int elem_lp_blocks(const DeviceMesh& m);
 cudaError_t launch_elem_lp(const DeviceMesh& m, const ElemLpArgs& a, int bf16, cudaStream_t s);
 // FP32 inner operator with the contractions on the tensor cores (3xTF32 mma.sync), order 7 only.
 bool elem_tc_supported(const DeviceMesh& m);
-int elem_tc_blocks(const DeviceMesh& m);
 cudaError_t launch_elem_tc(const DeviceMesh& m, const ElemLpArgs& a, cudaStream_t s);
 cudaError_t launch_residual(const DeviceMesh& m, const double* b, const double* ax, double* r, double* partials,
                             unsigned* ticket, double* out, cudaStream_t s);

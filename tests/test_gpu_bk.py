@@ -3,8 +3,8 @@
 ceedbp_bk_apply computes w^e = A^e u^e (or B^e u^e) for every element without
 Q, Q^T or the Dirichlet mask; the oracle builds each element matrix by full
 quadrature and multiplies.  Tolerance 1e-12 relative (2-norm over all
-elements), for every BP, both arithmetics of BP5/BP6 and the recomputed
-factors.
+elements), for every BP, both arithmetics of BP1/BP3/BP5/BP6 and the
+recomputed factors.
 """
 import numpy as np
 import pytest
@@ -43,6 +43,9 @@ def _oracle_bk(bp, dims, N, uL):
     (6, 3, (2, 2, 1), {}),
     (5, 3, (2, 2, 2), {"arith": pkg.ARITH_DF64}), (5, 7, (3, 1, 1), {"arith": pkg.ARITH_DF64}),
     (6, 5, (1, 2, 1), {"arith": pkg.ARITH_DF64}),
+    (1, 7, (2, 1, 2), {}), (3, 7, (2, 2, 1), {}), (3, 9, (1, 1, 2), {}), (1, 15, (1, 1, 1), {}),
+    (1, 3, (2, 1, 2), {"arith": pkg.ARITH_DF64}), (1, 7, (1, 2, 1), {"arith": pkg.ARITH_DF64}),
+    (3, 5, (2, 1, 1), {"arith": pkg.ARITH_DF64}), (3, 7, (2, 1, 2), {"arith": pkg.ARITH_DF64}),
     (5, 5, (2, 1, 2), {"geom": pkg.GEOM_RECOMPUTE}), (6, 3, (1, 1, 2), {"geom": pkg.GEOM_RECOMPUTE}),
 ])
 def test_bk_apply_matches_element_matrices(bp, N, dims, kw):
