@@ -130,7 +130,7 @@ constexpr int elem_threads() {
   return (((256 / (Q * Q * NC) < 1 ? 1 : 256 / (Q * Q * NC)) * Q * Q + 31) / 32) * 32;
 }
 
-template <int P1, int Q, bool COLLOC, int KIND, int NC>
+template <int P1, int Q, bool COLLOC, int KIND, int NC, bool BATCH = false>
 __global__ void __launch_bounds__(elem_threads<Q, NC>()) elem_kernel(const DeviceMesh m, const ElemArgs a,
                                                                      const int eb) {
   using S = ElemShape<P1, Q, COLLOC>;
@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(elem_threads<Q, NC>()) elem_kernel(const Devic
   int64_t e0 = int64_t(blockIdx.x) * eb;
   int nact = m.nelem - e0 < eb ? int(m.nelem - e0) : eb;
   int prob = 0;
-  if (a.blk_prob != nullptr) {  // batched: this block holds elements of one problem
+  if constexpr (BATCH) {  // batched: this block holds elements of one problem (block tables)
     prob = a.blk_prob[blockIdx.x];
     if (!a.bst[prob].c.active) return;
     e0 = a.blk_e0[blockIdx.x];
@@ -379,11 +379,9 @@ __global__ void __launch_bounds__(elem_threads<Q, NC>()) elem_kernel(const Devic
     }
   }
 
-  if constexpr (NC == 1) {
-    if (a.blk_prob != nullptr) {  // per-problem alpha from a segmented last-block reduction
-      batch_alpha(dot, a.partials, a.prob_blk0, a.prob_nblk, a.bst, prob, red);
-      return;
-    }
+  if constexpr (BATCH && NC == 1) {  // per-problem alpha from a segmented last-block reduction
+    batch_alpha(dot, a.partials, a.prob_blk0, a.prob_nblk, a.bst, prob, red);
+    return;
   }
   if (a.partials != nullptr) {
     if (grid_sum_last<NC>(dot, a.partials, gridDim.x, blockIdx.x, &a.state->ticket[kTicketApply], red)) {
@@ -411,19 +409,29 @@ __global__ void __launch_bounds__(elem_threads<Q, NC>()) elem_kernel(const Devic
   }
 }
 
-// Launch one instantiation.
-template <int P1, int Q, bool COLLOC, int KIND, int NC>
-cudaError_t launch_elem_t(const DeviceMesh& m, const ElemArgs& a, cudaStream_t s) {
+// Launch one instantiation of the kernel.
+template <int P1, int Q, bool COLLOC, int KIND, int NC, bool BATCH>
+cudaError_t launch_elem_b(const DeviceMesh& m, const ElemArgs& a, cudaStream_t s) {
   const int eb = elem_per_block<P1, Q, COLLOC, NC>();
   const int nthreads = ((eb * Q * Q + 31) / 32) * 32;
   const size_t smem = elem_smem_bytes<P1, Q, COLLOC, NC>(eb);
-  auto kern = elem_kernel<P1, Q, COLLOC, KIND, NC>;
+  auto kern = elem_kernel<P1, Q, COLLOC, KIND, NC, BATCH>;
   // set once per instantiation (not a stream operation; kept out of graph capture)
   static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (attr != cudaSuccess) return attr;
-  const int64_t blocks = a.blk_prob != nullptr ? int64_t(a.batch_blocks) : (m.nelem + eb - 1) / eb;
+  const int64_t blocks = BATCH ? int64_t(a.batch_blocks) : (m.nelem + eb - 1) / eb;
   kern<<<unsigned(blocks), nthreads, smem, s>>>(m, a, eb);
   return cudaGetLastError();
+}
+
+// Launch one instantiation (batched solves take the block-table variant: collocated stiffness,
+// one component).
+template <int P1, int Q, bool COLLOC, int KIND, int NC>
+cudaError_t launch_elem_t(const DeviceMesh& m, const ElemArgs& a, cudaStream_t s) {
+  if constexpr (COLLOC && KIND == kStiff && NC == 1) {
+    if (a.blk_prob != nullptr) return launch_elem_b<P1, Q, COLLOC, KIND, NC, true>(m, a, s);
+  }
+  return launch_elem_b<P1, Q, COLLOC, KIND, NC, false>(m, a, s);
 }
 
 template <int P1, int Q, bool COLLOC, int NC>

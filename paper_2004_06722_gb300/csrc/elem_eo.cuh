@@ -48,8 +48,9 @@ __device__ __forceinline__ int eo_node(int i, int j, int k, int bi, int bj, int 
 }
 
 // HELM: the Helmholtz term beta B u of Eq. (17) is compiled in only for beta != 0, so the plain
-// stiffness kernel carries no extra registers or branches.
-template <int P1, int NC, bool HELM>
+// stiffness kernel carries no extra registers or branches.  BATCH: the block tables and per-problem
+// reductions of batched solves (one component), likewise compiled in only where used.
+template <int P1, int NC, bool HELM, bool BATCH = false>
 __global__ void elem_eo_kernel(const DeviceMesh m, const ElemArgs a, const int eb) {
   using S = EoShape<P1>;
   constexpr int H = S::H, H3 = S::H3, P3 = S::P3, HALF = S::HALF;
@@ -68,7 +69,7 @@ __global__ void elem_eo_kernel(const DeviceMesh m, const ElemArgs a, const int e
   int64_t e0 = int64_t(blockIdx.x) * eb;
   int nact = m.nelem - e0 < eb ? int(m.nelem - e0) : eb;
   int prob = 0;
-  if (a.blk_prob != nullptr) {  // batched: this block holds elements of one problem
+  if constexpr (BATCH) {  // batched: this block holds elements of one problem
     prob = a.blk_prob[blockIdx.x];
     if (!a.bst[prob].c.active) return;
     e0 = a.blk_e0[blockIdx.x];
@@ -303,11 +304,9 @@ __global__ void elem_eo_kernel(const DeviceMesh m, const ElemArgs a, const int e
     }
   }
 
-  if constexpr (NC == 1) {
-    if (a.blk_prob != nullptr) {  // per-problem alpha from a segmented last-block reduction
-      batch_alpha(dot, a.partials, a.prob_blk0, a.prob_nblk, a.bst, prob, red);
-      return;
-    }
+  if constexpr (BATCH && NC == 1) {  // per-problem alpha from a segmented last-block reduction
+    batch_alpha(dot, a.partials, a.prob_blk0, a.prob_nblk, a.bst, prob, red);
+    return;
   }
   if (a.partials != nullptr) {
     if (grid_sum_last<NC>(dot, a.partials, gridDim.x, blockIdx.x, &a.state->ticket[kTicketApply], red)) {
@@ -335,21 +334,24 @@ __global__ void elem_eo_kernel(const DeviceMesh m, const ElemArgs a, const int e
   }
 }
 
-template <int P1, int NC, bool HELM>
+template <int P1, int NC, bool HELM, bool BATCH = false>
 cudaError_t launch_elem_eo_h(const DeviceMesh& m, const ElemArgs& a, cudaStream_t s) {
   const int eb = elem_eo_per_block<P1, NC>();
   const int nthreads = ((eb * EoShape<P1>::H3 + 31) / 32) * 32;
   const size_t smem = elem_eo_smem_bytes<P1, NC>(eb);
-  auto kern = elem_eo_kernel<P1, NC, HELM>;
+  auto kern = elem_eo_kernel<P1, NC, HELM, BATCH>;
   static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (attr != cudaSuccess) return attr;
-  const int64_t blocks = a.blk_prob != nullptr ? int64_t(a.batch_blocks) : (m.nelem + eb - 1) / eb;
+  const int64_t blocks = BATCH ? int64_t(a.batch_blocks) : (m.nelem + eb - 1) / eb;
   kern<<<unsigned(blocks), nthreads, smem, s>>>(m, a, eb);
   return cudaGetLastError();
 }
 
 template <int P1, int NC>
 cudaError_t launch_elem_eo_t(const DeviceMesh& m, const ElemArgs& a, cudaStream_t s) {
+  if constexpr (NC == 1) {
+    if (a.blk_prob != nullptr) return launch_elem_eo_h<P1, 1, false, true>(m, a, s);
+  }
   return a.beta != 0.0 ? launch_elem_eo_h<P1, NC, true>(m, a, s) : launch_elem_eo_h<P1, NC, false>(m, a, s);
 }
 

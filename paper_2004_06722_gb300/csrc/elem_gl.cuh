@@ -65,15 +65,8 @@ __global__ void __launch_bounds__(elem_gl_threads<P1, Q>()) elem_gl_kernel(const
 
   const int tid = threadIdx.x;
   const int slot = tid / QQ, t = tid - slot * QQ;
-  int64_t e0 = int64_t(blockIdx.x) * EB;
-  int nact = m.nelem - e0 < EB ? int(m.nelem - e0) : EB;
-  int prob = 0;
-  if (a.blk_prob != nullptr) {  // batched tables (one problem per block), as elem_kernel
-    prob = a.blk_prob[blockIdx.x];
-    if (!a.bst[prob].c.active) return;
-    e0 = a.blk_e0[blockIdx.x];
-    nact = a.blk_n[blockIdx.x];
-  }
+  const int64_t e0 = int64_t(blockIdx.x) * EB;
+  const int nact = m.nelem - e0 < EB ? int(m.nelem - e0) : EB;
   const int64_t e = e0 + slot;
   const bool active = slot < nact;
 
@@ -244,10 +237,6 @@ __global__ void __launch_bounds__(elem_gl_threads<P1, Q>()) elem_gl_kernel(const
     }
   }
 
-  if (a.blk_prob != nullptr) {
-    batch_alpha(dot, a.partials, a.prob_blk0, a.prob_nblk, a.bst, prob, red);
-    return;
-  }
   if (a.partials != nullptr) {
     if (grid_sum_last<1>(dot, a.partials, gridDim.x, blockIdx.x, &a.state->ticket[kTicketApply], red)) {
       if (threadIdx.x == 0) {
@@ -277,7 +266,7 @@ cudaError_t launch_elem_gl_h(const DeviceMesh& m, const ElemArgs& a, cudaStream_
   auto kern = elem_gl_kernel<P1, Q, KIND, HELM>;
   static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (attr != cudaSuccess) return attr;
-  const int64_t blocks = a.blk_prob != nullptr ? int64_t(a.batch_blocks) : (m.nelem + EB - 1) / EB;
+  const int64_t blocks = (m.nelem + EB - 1) / EB;
   kern<<<unsigned(blocks), elem_gl_threads<P1, Q>(), smem, s>>>(m, a);
   return cudaGetLastError();
 }
