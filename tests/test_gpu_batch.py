@@ -73,13 +73,14 @@ def test_batch_without_graphs_and_single_member(arith):
     batch.close()
 
 
-def test_fp64_batch_every_small_member_against_oracle():
-    """FP64 arithmetic: every member of a 16-problem batch (k <= 4, orders 3, 5, 7) solved to
-    1e-10 against the oracle's PCG (iterations within 1, both residuals at the tolerance, solution
-    difference printed and bounded) and against its own single-problem FP64 solve."""
-    draws, probs, rhs = _problems(16, 4, pkg.ARITH_FP64, seed=11)
+@pytest.mark.parametrize("arith", [pkg.ARITH_FP64, pkg.ARITH_DF64])
+def test_batch_every_small_member_against_oracle(arith):
+    """Every member of a 16-problem batch (k <= 4, orders 3, 5, 7) solved to 1e-10 against the
+    oracle's PCG (iterations within 1, both residuals at the tolerance, solution difference printed
+    and bounded) and against its own single-problem solve, in both arithmetics."""
+    draws, probs, rhs = _problems(16, 4, arith, seed=11)
     assert {q["N"] for q in draws} == {3, 5, 7}
-    batch = pkg.Batch(probs, arith=pkg.ARITH_FP64)
+    batch = pkg.Batch(probs, arith=arith)
     xs, infos = batch.solve([b for b, _ in rhs], tol=1e-10)
     worst = 0.0
     for k, q in enumerate(draws):
@@ -94,7 +95,7 @@ def test_fp64_batch_every_small_member_against_oracle():
         assert err <= 1e-8, (k, q, err)
         x1, i1 = rhs[k][1].solve(rhs[k][0], tol=1e-10)
         assert abs(infos[k]["iters"][0] - i1["iters"][0]) <= 1
-    print(f"FP64 batch, 16 members vs oracle: worst |x - x_oracle| / |x_oracle| = {worst:.2e}")
+    print(f"batch arith={arith}, 16 members vs oracle: worst |x - x_oracle| / |x_oracle| = {worst:.2e}")
     batch.close()
 
 
