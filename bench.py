@@ -61,6 +61,7 @@ def parse_args():
     ap.add_argument("--bp", type=int, default=3, help="bake-off problem of the bp-point workload")
     ap.add_argument("--bps", default="1,3,5", help="bake-off problems of the bp-sweep workload")
     ap.add_argument("--bk-bps", default="", help="element operators of the bk-sweep workload (default: 5)")
+    ap.add_argument("--bk-orders", default="1,2,3,5,7,9,11,15", help="orders N of the bk-sweep workload")
     ap.add_argument("--df-tile", default=None,
                     help="pin the pair kernel's shape 'eb,schedule,seq' instead of the autotuner's choice")
     ap.add_argument("--geom", choices=["stored", "recompute"], default="stored",
@@ -871,7 +872,7 @@ def bk_flops(bp: int, N: int) -> int:
 
 def run_bk_sweep(args):
     """Unassembled BK kernels (the element operators of the BPs in --bps, no Q, Q^T or mask;
-    ceedbp_bk_apply) at N in {1, 2, 3, 5, 7, 9, 11, 15}, FP64 and FP32 pairs (where built), on E = 2^k boxes
+    ceedbp_bk_apply) at N in --bk-orders (default {1, 2, 3, 5, 7, 9, 11, 15}), FP64 and FP32 pairs (where built), on E = 2^k boxes
     (k <= 21) with n = E N^3 from ~1e3 to ~1e8 (k in steps of 2): time per apply (CUDA events over
     `--sweep-iters` applies after 3 warm-ups), algorithmic GFLOP/s (bk_flops per element), DOFs/s and r_max,
     n_0.8 per (BK, arith, N).  The default runs BK5; --bk-bps 1,3,5 adds BK1 and BK3."""
@@ -882,12 +883,11 @@ def run_bk_sweep(args):
     from synth import box_dims, uniform_pm1
     reps = args.sweep_iters
     bps = [int(v) for v in (args.bk_bps or "5").split(",")]
+    orders = [int(v) for v in args.bk_orders.split(",")]
     out = {}
     for bp in bps:
         for name, arith in (("fp64", pkg.ARITH_FP64), ("df64", pkg.ARITH_DF64)):
-            for N in (1, 2, 3, 5, 7, 9, 11, 15):
-                if arith == pkg.ARITH_DF64 and bp in (1, 3) and N > 11:
-                    continue  # the pair path of BK1/BK3 is built up to order 11
+            for N in orders:
                 p1 = N + 1
                 ns, rates, gflops, tpp = [], [], [], []
                 k = 0

@@ -67,8 +67,8 @@ enum {
   CEEDBP_ARITH_FP64 = 0, /* native FP64 instructions */
   CEEDBP_ARITH_DF64 = 1  /* FP64-accurate pairs of FP32 numbers (hi + lo, ~2^-46 relative per
                             value) on the FP32 pipe, which the GB300 issues 63x faster than
-                            FP64; BP5 and BP6, and BP1 and BP3 up to order 11 (EUNSUPPORTED
-                            otherwise).  One apply matches the FP64 path to about 2e-13
+                            FP64; BP1, BP3, BP5 and BP6 (EUNSUPPORTED for BP2 and BP4).
+                            One apply matches the FP64 path to about 2e-13
                             relative and the FP64 oracle to below 1e-12. */
 };
 

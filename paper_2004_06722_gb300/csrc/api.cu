@@ -132,9 +132,8 @@ ceedbp_status setup_impl(ceedbp_ctx* c, const double* coords, const int64_t* l2g
     return fail(c, CEEDBP_EINVAL, "problem too large for 32-bit local indices (E p1^3 and nglobal must stay below 2^31)");
   const bool masked = P.bp != 1 && P.bp != 2 && dirichlet != nullptr;
   if (P.arith != CEEDBP_ARITH_FP64 && P.arith != CEEDBP_ARITH_DF64) return fail(c, CEEDBP_EINVAL, "unknown arith");
-  if (P.arith == CEEDBP_ARITH_DF64 && !gll_quad && !((P.bp == 1 || P.bp == 3) && P.order <= 11))
-    return fail(c, CEEDBP_EUNSUPPORTED,
-                "the FP32-pair arithmetic is built for BP5 and BP6, and for BP1 and BP3 up to order 11");
+  if (P.arith == CEEDBP_ARITH_DF64 && !gll_quad && P.bp != 1 && P.bp != 3)
+    return fail(c, CEEDBP_EUNSUPPORTED, "the FP32-pair arithmetic is built for BP1, BP3, BP5 and BP6");
   c->arith = P.arith;
   if (P.geom != CEEDBP_GEOM_STORED && P.geom != CEEDBP_GEOM_RECOMPUTE) return fail(c, CEEDBP_EINVAL, "unknown geom");
   const bool recompute = P.geom == CEEDBP_GEOM_RECOMPUTE;

@@ -326,9 +326,9 @@ cudaError_t launch_dfgl_p(const DeviceMesh& m, const ElemDfArgs& a, cudaStream_t
 
 }  // namespace
 
-// Orders 1..11 (larger q^3 tiles of pairs leave too few registers and too little shared memory).
+// Orders 1..15 (at order 15 one element of q^3 pair tiles takes 150 KB of shared memory).
 bool elem_dfgl_supported(const DeviceMesh& m) {
-  return !m.colloc && m.ncomp == 1 && (m.bp == 1 || m.bp == 3) && m.p1 >= 2 && m.p1 <= 12;
+  return !m.colloc && m.ncomp == 1 && (m.bp == 1 || m.bp == 3) && m.p1 >= 2 && m.p1 <= 16;
 }
 
 int elem_dfgl_blocks(const DeviceMesh& m) {
@@ -351,6 +351,10 @@ cudaError_t launch_elem_dfgl(const DeviceMesh& m, const ElemDfArgs& a, cudaStrea
     case 10: return launch_dfgl_p<10>(m, a, s);
     case 11: return launch_dfgl_p<11>(m, a, s);
     case 12: return launch_dfgl_p<12>(m, a, s);
+    case 13: return launch_dfgl_p<13>(m, a, s);
+    case 14: return launch_dfgl_p<14>(m, a, s);
+    case 15: return launch_dfgl_p<15>(m, a, s);
+    case 16: return launch_dfgl_p<16>(m, a, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -72,7 +72,7 @@ def test_setup_without_gpu_fails_loudly(lib):
     (5, 7, 1 << 22, 64, 0, 0, pkg.EINVAL),           # E p1^3 beyond 32-bit local indices
     (5, 3, 1, 64, 5, 0, pkg.EINVAL),                 # unknown arithmetic
     (4, 3, 1, 64, pkg.ARITH_DF64, 0, pkg.EUNSUPPORTED),  # pair arithmetic: not BP2/BP4
-    (3, 12, 1, 2197, pkg.ARITH_DF64, 0, pkg.EUNSUPPORTED),  # pair arithmetic for BP1/BP3 up to order 11
+    (2, 3, 1, 64, pkg.ARITH_DF64, 0, pkg.EUNSUPPORTED),  # pair arithmetic: not BP2/BP4
     (5, 3, 1, 64, 0, 7, pkg.EINVAL),                 # unknown geometry mode
     (3, 3, 1, 64, 0, pkg.GEOM_RECOMPUTE, pkg.EUNSUPPORTED),  # recomputed factors are BP5/BP6 only
     (6, 15, 1, 4096, 0, pkg.GEOM_RECOMPUTE, pkg.EUNSUPPORTED),  # BP6 tile too large at p1 = 16
