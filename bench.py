@@ -346,7 +346,7 @@ def measure(pkg, args, mesh, arith, device, rank, world, dist, geom=0):
     if arith != pkg.ARITH_FP64:
         eb, sched, seq = op.tile_info()
         out["roofline"]["tile"] = {"elements_per_block": eb,
-                                   "schedule": ["G ring (cp.async)", "G staged (bulk copy)", "pipelined sequences"][sched],
+                                   "schedule": ["G ring (cp.async)", "G staged (bulk copy)", "pipelined sequences", "even-odd octets"][sched],
                                    "elements_per_sequence": seq}
     op.close()
     return out

@@ -336,15 +336,21 @@ ceedbp_status ceedbp_bk_apply(ceedbp_ctx* ctx, const double* uL, double* wL);
  * (0: G fetched two slabs ahead into a ring by per-thread asynchronous copies;
  * 1: the element's G staged in shared memory by one bulk asynchronous copy;
  * 2: software-pipelined sequences, each group of p1^2 threads working through
- * `seq` consecutive elements while fetching the next one's data), and seq
- * (1 for schedules 0 and 1).  Outputs are 0 (seq 1) for contexts without the
- * pair path; any output pointer may be NULL. */
+ * `seq` consecutive elements while fetching the next one's data; 3: the
+ * even-odd form of the 1D contractions (Eq. (37)) on pairs, one thread per
+ * mirror octet of nodes, pipelined sequences of `seq` elements per group of
+ * p1^3/8 threads -- BP5 at odd orders 3..11), and seq (1 for schedules 0 and
+ * 1).  Outputs are 0 (seq 1) for contexts without the pair path; any output
+ * pointer may be NULL. */
 ceedbp_status ceedbp_tile_info(const ceedbp_ctx* ctx, int* elems_per_block, int* schedule, int* seq);
 
 /* Replace the autotuner's choice by one of the shapes it times (same meaning
- * as ceedbp_tile_info; seq is ignored for schedules 0 and 1).  Every shape
- * computes the same element results; the fused (p, A p) may differ in the last
- * bits because the summation order of the block partials changes.  Returns
+ * as ceedbp_tile_info; seq is ignored for schedules 0 and 1).  The shapes of
+ * schedules 0..2 compute the same element results bit for bit, and so do the
+ * shapes of schedule 3 among themselves; schedule 3 rounds differently from
+ * 0..2 (the results agree to the pair arithmetic's accuracy, about 1e-13
+ * relative).  The fused (p, A p) may differ in the last bits between shapes
+ * because the summation order of the block partials changes.  Returns
  * CEEDBP_EINVAL for a shape that is not launchable at this order,
  * CEEDBP_EUNSUPPORTED on a context without the pair path.  Synchronises the
  * context's stream and drops its captured CUDA graphs. */

@@ -307,7 +307,8 @@ class Operator:
 
     def tile_info(self):
         """(elements per block, schedule, elements per sequence) chosen by the setup autotuner for the
-        pair kernel; schedule 0 = G ring, 1 = G staged by a bulk copy, 2 = pipelined sequences."""
+        pair kernel; schedule 0 = G ring, 1 = G staged by a bulk copy, 2 = pipelined sequences,
+        3 = even-odd octets in pipelined sequences (BP5, odd orders 3..11)."""
         eb, st, seq = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
         _check(self.lib.ceedbp_tile_info(self.ctx, ctypes.byref(eb), ctypes.byref(st), ctypes.byref(seq)),
                self.ctx)

@@ -67,6 +67,19 @@ namespace {
 
 thread_local std::string g_setup_error;
 
+// Shapes of the BK5/BK6 pair kernel: the direct schedules 0..2 (elem_df_tile_candidates), then the
+// even-odd kernel (schedule 3) where it is built; batched groups launch with block tables, which
+// only the direct schedules take.
+int pair_shape_candidates(const ceedbp_ctx* c, const DeviceMesh& m, int* eb, int* st, int* ns, int cap) {
+  int n = elem_df_tile_candidates(m, eb, st, ns, cap, true);
+  if (!c->pipelined_only) {
+    const int k = elem_dfeo_candidates(m, eb + n, ns + n, cap - n);
+    for (int q = 0; q < k; ++q) st[n + q] = 3;
+    n += k;
+  }
+  return n;
+}
+
 ceedbp_status fail(ceedbp_ctx* c, ceedbp_status st, const std::string& msg) {
   if (c) c->err = msg;
   else g_setup_error = msg;
@@ -352,7 +365,7 @@ ceedbp_status setup_impl(ceedbp_ctx* c, const double* coords, const int64_t* l2g
     CK(c, cudaStreamSynchronize(s));
     // autotuner: elements per block and G staging of the pair kernel, timed on this mesh
     int cand_eb[32], cand_st[32], cand_ns[32];
-    int ncand = elem_df_tile_candidates(m, cand_eb, cand_st, cand_ns, 32, true);
+    int ncand = pair_shape_candidates(c, m, cand_eb, cand_st, cand_ns, 32);
     if (c->pipelined_only) {  // keep the pipelined shapes when there are any
       int np = 0;
       for (int k = 0; k < ncand; ++k)
@@ -364,35 +377,55 @@ ceedbp_status setup_impl(ceedbp_ctx* c, const double* coords, const int64_t* l2g
       if (np > 0) ncand = np;
     }
     if (ncand == 0) return fail(c, CEEDBP_EUNSUPPORTED, "no launchable shape for the pair kernel at this order");
-    float best = 1e30f;
-    int best_k = 0;
-    for (int k = 0; k < ncand && ncand > 1; ++k) {
-      m.tune_eb = cand_eb[k];
-      m.tune_stage = cand_st[k];
-      m.tune_ns = cand_ns[k];
-      {  // warm-up of this shape
-        const cudaError_t e = launch_elem_df(m, a, s);
-        if (e != cudaSuccess)
-          return cuda_fail(c, e, ("pair kernel shape eb=" + std::to_string(m.tune_eb) + " schedule=" +
-                                  std::to_string(m.tune_stage) + " seq=" + std::to_string(m.tune_ns)).c_str());
+    // The launches are timed as a solve makes them: with the fused (u, w) and its last-block
+    // grid reduction, whose cost grows with the number of blocks (shapes with short sequences
+    // have more).  The state lets every launch run to the end (fixed, active, never stopping);
+    // it is zeroed again after tuning.
+    {
+      SolveState hs{};
+      hs.ncomp = c->ncomp;
+      hs.fixed = 1;
+      for (int q = 0; q < c->ncomp; ++q) {
+        hs.c[q].active = 1;
+        hs.c[q].rz = 1.0;
       }
-      CK(c, cudaEventRecord(c->ev0, s));
-      for (int r = 0; r < 3; ++r) CK(c, launch_elem_df(m, a, s));
-      CK(c, cudaEventRecord(c->ev1, s));
-      CK(c, cudaEventSynchronize(c->ev1));
-      float ms = 0.0f;
-      CK(c, cudaEventElapsedTime(&ms, c->ev0, c->ev1));
-      if (ms < best) {
-        best = ms;
-        best_k = k;
+      CK(c, cudaMemcpyAsync(c->d_state, &hs, sizeof(hs), cudaMemcpyHostToDevice, s));
+      CK(c, cudaStreamSynchronize(s));
+    }
+    a.partials = c->d_part_apply;
+    a.state = c->d_state;
+    // two passes over the candidates, each shape's best of the two (the first pass also warms
+    // the clocks and caches that the first candidates would otherwise be timed without)
+    std::vector<float> best_ms(size_t(ncand), 1e30f);
+    for (int pass = 0; pass < 2 && ncand > 1; ++pass) {
+      for (int k = 0; k < ncand; ++k) {
+        m.tune_eb = cand_eb[k];
+        m.tune_stage = cand_st[k];
+        m.tune_ns = cand_ns[k];
+        {  // warm-up of this shape
+          const cudaError_t e = launch_elem_df(m, a, s);
+          if (e != cudaSuccess)
+            return cuda_fail(c, e, ("pair kernel shape eb=" + std::to_string(m.tune_eb) + " schedule=" +
+                                    std::to_string(m.tune_stage) + " seq=" + std::to_string(m.tune_ns)).c_str());
+        }
+        CK(c, cudaEventRecord(c->ev0, s));
+        for (int r = 0; r < 3; ++r) CK(c, launch_elem_df(m, a, s));
+        CK(c, cudaEventRecord(c->ev1, s));
+        CK(c, cudaEventSynchronize(c->ev1));
+        float ms = 0.0f;
+        CK(c, cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+        best_ms[size_t(k)] = std::min(best_ms[size_t(k)], ms);
       }
     }
+    int best_k = 0;
+    for (int k = 1; k < ncand; ++k)
+      if (best_ms[size_t(k)] < best_ms[size_t(best_k)]) best_k = k;
     m.tune_eb = cand_eb[best_k];
     m.tune_stage = cand_st[best_k];
     m.tune_ns = cand_ns[best_k];
     CK(c, launch_elem_df(m, a, s));  // the chosen shape, launched once outside any capture
     CK(c, cudaStreamSynchronize(s));
-    CK(c, cudaMemsetAsync(&c->d_state->fault, 0, sizeof(int), s));
+    CK(c, cudaMemsetAsync(c->d_state, 0, sizeof(SolveState), s));
   }
   // the static scratch of ceedbp_apply_noalloc: its device address on this device, looked up here
   CK(c, noalloc_scratch_refresh());
@@ -909,7 +942,7 @@ ceedbp_status ceedbp_tile_info(const ceedbp_ctx* c, int* eb, int* staged, int* s
   const bool df = c->arith == CEEDBP_ARITH_DF64;
   if (eb) *eb = df ? c->mesh.tune_eb : 0;
   if (staged) *staged = df ? c->mesh.tune_stage : 0;
-  if (seq) *seq = df && c->mesh.tune_stage == 2 ? c->mesh.tune_ns : 1;
+  if (seq) *seq = df && c->mesh.tune_stage >= 2 ? c->mesh.tune_ns : 1;
   return CEEDBP_OK;
 }
 
@@ -1000,10 +1033,10 @@ ceedbp_status ceedbp_set_tile(ceedbp_ctx* c, int eb, int schedule, int seq) {
   if (c->arith != CEEDBP_ARITH_DF64 || !c->colloc)
     return fail(c, CEEDBP_EUNSUPPORTED, "tile shapes belong to the pair path of BP5/BP6");
   int cand_eb[32], cand_st[32], cand_ns[32];
-  const int ncand = elem_df_tile_candidates(c->mesh, cand_eb, cand_st, cand_ns, 32, true);
+  const int ncand = pair_shape_candidates(c, c->mesh, cand_eb, cand_st, cand_ns, 32);
   int hit = -1;
   for (int k = 0; k < ncand; ++k)
-    if (cand_eb[k] == eb && cand_st[k] == schedule && (schedule != 2 || cand_ns[k] == seq)) hit = k;
+    if (cand_eb[k] == eb && cand_st[k] == schedule && (schedule < 2 || cand_ns[k] == seq)) hit = k;
   if (hit < 0) return fail(c, CEEDBP_EINVAL, "not a launchable shape of the pair kernel at this order");
   cudaStream_t s = c->stream;
   CK(c, cudaStreamSynchronize(s));

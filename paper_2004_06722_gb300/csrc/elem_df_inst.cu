@@ -56,6 +56,7 @@ cudaError_t set_df_dconst(int p1, const dfloat* host, cudaStream_t s) {
 
 cudaError_t launch_elem_df(const DeviceMesh& m, const ElemDfArgs& a, cudaStream_t s) {
   if (!m.colloc) return launch_elem_dfgl(m, a, s);  // BP1 / BP3 (Gauss quadrature)
+  if (m.tune_stage == 3) return launch_elem_dfeo(m, a, s);  // even-odd BK5
   const int p1 = m.p1;
   if (df_has_a(p1)) return launch_elem_df_a(m, a, s);
   if (df_has_b(p1)) return launch_elem_df_b(m, a, s);

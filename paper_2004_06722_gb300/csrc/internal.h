@@ -155,6 +155,11 @@ struct ElemDfArgs;
 int elem_df_tile_candidates(const DeviceMesh& m, int* eb, int* stage, int* ns, int cap, bool pipelined);
 cudaError_t set_df_dconst(int p1, const dfloat* host, cudaStream_t s);
 cudaError_t launch_elem_df(const DeviceMesh& m, const ElemDfArgs& a, cudaStream_t s);
+// BK5 on FP32 pairs with the even-odd decomposition (schedule 3 of the pair kernel): one
+// component, even p1 in 4..12, not for batched launches.
+bool elem_dfeo_supported(const DeviceMesh& m);
+int elem_dfeo_candidates(const DeviceMesh& m, int* eb, int* ns, int cap);
+cudaError_t launch_elem_dfeo(const DeviceMesh& m, const ElemDfArgs& a, cudaStream_t s);
 // BP1/BP3 (Gauss quadrature) on FP32 pairs; a.D holds the pair tables J [q][p1] then Dq [q][q].
 bool elem_dfgl_supported(const DeviceMesh& m);
 int elem_dfgl_blocks(const DeviceMesh& m);

@@ -109,11 +109,15 @@ def test_df64_x0_restart():
     assert _rel(x2.cpu().numpy(), xr) < 1e-8
 
 
-def test_df64_sampled_rows_largest_n7():
-    """The pair path at the bench size (E = 2^18, N = 7, autotuned shape) on at least 200 rows
-    (vertices, edges, faces and interiors of probe elements, the last element among them)."""
+@pytest.mark.parametrize("tile", [None, (2, 2, 16), (1, 3, 16)])
+def test_df64_sampled_rows_largest_n7(tile):
+    """The pair path at the bench size (E = 2^18, N = 7; the autotuned shape, the pipelined direct
+    schedule and the even-odd schedule) on at least 200 rows (vertices, edges, faces and interiors
+    of probe elements, the last element among them)."""
     dims, N = box_dims(18), 7
     op = _box(5, dims, N)
+    if tile is not None:
+        op.set_tile(*tile)
     n = op.nglobal
     u_h = uniform_pm1(9, np.arange(n))
     w = op.apply(torch.from_numpy(u_h).cuda())
@@ -164,11 +168,71 @@ def test_pipelined_schedule_parity_and_same_bits(bp, N, dims):
     assert ei.value.status == pkg.EINVAL
 
 
+EVEN_ODD = [(1, 4), (1, 8), (1, 16), (2, 8), (4, 8), (8, 8), (16, 8), (32, 4)]
+
+
+@pytest.mark.parametrize("N,dims", [(3, (3, 2, 5)), (5, (3, 3, 2)), (7, (5, 3, 3)), (9, (3, 1, 2)),
+                                    (11, (2, 1, 2))])
+def test_even_odd_schedule_parity(N, dims):
+    """The even-odd pair kernel (schedule 3): every launchable shape (ragged last sequence: E is
+    not a multiple of eb * seq) matches the oracle to 1e-12; its shapes agree bit for bit among
+    themselves, and with the direct schedule to the pair arithmetic's accuracy."""
+    op = _box(5, dims, N)
+    ref = BakeoffProblem(5, *dims, N, amp=0.05)
+    u = _vec(op.nglobal, 1, 13)
+    ut = torch.from_numpy(u).cuda()
+    w_ref = ref.apply(u)
+    outs = []
+    for eb, seq in EVEN_ODD:
+        try:
+            op.set_tile(eb, 3, seq)
+        except pkg.CeedbpError as e:
+            assert e.status == pkg.EINVAL
+            continue
+        assert op.tile_info() == (eb, 3, seq)
+        w = op.apply(ut).cpu().numpy()
+        err = _rel(w, w_ref)
+        assert err < APPLY_TOL, (eb, seq, err)
+        outs.append(w)
+    assert len(outs) >= 3
+    for w in outs[1:]:
+        np.testing.assert_array_equal(w, outs[0])
+    op.set_tile(1, 0)
+    w0 = op.apply(ut).cpu().numpy()
+    assert _rel(outs[0], w0) < 1e-12
+
+
+def test_even_odd_schedule_not_offered_where_not_built():
+    """Schedule 3 is BP5 at odd orders 3..11: BP6 and even orders reject it."""
+    for bp, N, dims in ((6, 3, (2, 2, 2)), (5, 4, (2, 2, 2)), (5, 1, (2, 2, 2))):
+        op = _box(bp, dims, N)
+        with pytest.raises(pkg.CeedbpError) as ei:
+            op.set_tile(1, 3, 8)
+        assert ei.value.status == pkg.EINVAL
+        assert op.tile_info()[1] != 3
+        op.close()
+
+
 @pytest.mark.parametrize("bp,N,dims,tile", [(5, 7, (2, 2, 3), (1, 8)), (5, 3, (4, 3, 3), (2, 4)),
                                              (6, 3, (2, 2, 2), (1, 4))])
 def test_pipelined_schedule_solve_parity(bp, N, dims, tile):
     op = _box(bp, dims, N)
     op.set_tile(tile[0], 2, tile[1])
+    _solve_parity(op, bp, N, dims)
+
+
+@pytest.mark.parametrize("N,dims,tile", [(7, (2, 2, 3), (1, 8)), (3, (4, 3, 3), (8, 4)), (7, (3, 3, 2), (2, 4)),
+                                         (5, (3, 2, 2), (2, 16))])
+def test_even_odd_schedule_solve_parity(N, dims, tile):
+    """CG with the even-odd pair kernel against the oracle (orders up to 7: at higher orders on
+    meshes of a few elements the pair arithmetic's 1e-12 apply error, amplified by CG, moves the
+    final residual by more than the 1e-10 bar whatever the schedule)."""
+    op = _box(5, dims, N)
+    op.set_tile(tile[0], 3, tile[1])
+    _solve_parity(op, 5, N, dims)
+
+
+def _solve_parity(op, bp, N, dims):
     ref = BakeoffProblem(bp, *dims, N, amp=0.05)
     b = ref.rhs(_vec(op.nglobal, op.ncomp, 0))
     x, info = op.solve(torch.from_numpy(np.ascontiguousarray(b)).cuda(), tol=1e-8)
