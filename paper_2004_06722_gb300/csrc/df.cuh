@@ -117,6 +117,17 @@ struct SplitAcc {
   __device__ __forceinline__ dfloat result(float sigma) const {
     return dfloat{__fsub_rn(A, sigma), __fadd_rn(s, c)};
   }
+  // The accumulator after its first term: the sums of SplitAcc(sigma) followed by add(), less the
+  // additions of zero (which IEEE signed zeros keep the compiler from removing); equal results up
+  // to the sign of a zero.
+  __device__ __forceinline__ static SplitAcc first(float sigma, float dh, float dl, float xh, float xl) {
+    SplitAcc r(sigma);
+    const float an = __fmaf_rn(dh, xh, sigma);
+    r.s = __fmaf_rn(dh, xh, __fsub_rn(sigma, an));
+    r.c = __fmaf_rn(dl, xh, __fmul_rn(dh, xl));
+    r.A = an;
+    return r;
+  }
 };
 
 // ---- bulk asynchronous copy global -> shared with an mbarrier (Blackwell TMA unit)

@@ -313,9 +313,11 @@ __global__ void __launch_bounds__(256) __maxnreg__(kDfeoRegs<P1>) elem_dfeo_kern
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int L = o2[q >> 1] + o1[q & 1];  // lineoff(a2 * P1 + a1)
-          SplitAcc ae(sig1), ao(sig1);
+          const dfloat xp0 = Tp[L], xm0 = Tp[HALF + L];
+          SplitAcc ae = SplitAcc::first(sig1, ce[0].hi, ce[0].lo, xp0.hi, xp0.lo);
+          SplitAcc ao = SplitAcc::first(sig1, co[0].hi, co[0].lo, xm0.hi, xm0.lo);
 #pragma unroll
-          for (int n = 0; n < H; ++n) {
+          for (int n = 1; n < H; ++n) {
             const dfloat xp = Tp[L + n], xm = Tp[HALF + L + n];
             ae.add(ce[n].hi, ce[n].lo, xp.hi, xp.lo);
             ao.add(co[n].hi, co[n].lo, xm.hi, xm.lo);
@@ -335,14 +337,13 @@ __global__ void __launch_bounds__(256) __maxnreg__(kDfeoRegs<P1>) elem_dfeo_kern
         const dfloat ur = X0[c8], us = X1[ls], ut = X2[lt];
         const float um = fmaxf(fmaxf(fabsf(ur.hi), fabsf(us.hi)), fabsf(ut.hi));
         const float sg = splitter(gb * um);
-        SplitAcc wr(sg), ws(sg), wq(sg);
-        wr.add(g[0].hi, g[0].lo, ur.hi, ur.lo);
+        SplitAcc wr = SplitAcc::first(sg, g[0].hi, g[0].lo, ur.hi, ur.lo);
         wr.add(g[1].hi, g[1].lo, us.hi, us.lo);
         wr.add(g[2].hi, g[2].lo, ut.hi, ut.lo);
-        ws.add(g[1].hi, g[1].lo, ur.hi, ur.lo);
+        SplitAcc ws = SplitAcc::first(sg, g[1].hi, g[1].lo, ur.hi, ur.lo);
         ws.add(g[3].hi, g[3].lo, us.hi, us.lo);
         ws.add(g[4].hi, g[4].lo, ut.hi, ut.lo);
-        wq.add(g[2].hi, g[2].lo, ur.hi, ur.lo);
+        SplitAcc wq = SplitAcc::first(sg, g[2].hi, g[2].lo, ur.hi, ur.lo);
         wq.add(g[4].hi, g[4].lo, us.hi, us.lo);
         wq.add(g[5].hi, g[5].lo, ut.hi, ut.lo);
         X0[c8] = wr.result(sg);
@@ -406,9 +407,11 @@ __global__ void __launch_bounds__(256) __maxnreg__(kDfeoRegs<P1>) elem_dfeo_kern
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int L = o2[q >> 1] + o1[q & 1];  // lineoff(a2 * P1 + a1)
-          SplitAcc ae(sig), ao(sig);
+          const dfloat xp0 = Tp[L], xm0 = Tp[HALF + L];
+          SplitAcc ae = SplitAcc::first(sig, ce[0].hi, ce[0].lo, xp0.hi, xp0.lo);
+          SplitAcc ao = SplitAcc::first(sig, co[0].hi, co[0].lo, xm0.hi, xm0.lo);
 #pragma unroll
-          for (int n = 0; n < H; ++n) {
+          for (int n = 1; n < H; ++n) {
             const dfloat xp = Tp[L + n], xm = Tp[HALF + L + n];
             ae.add(ce[n].hi, ce[n].lo, xp.hi, xp.lo);
             ao.add(co[n].hi, co[n].lo, xm.hi, xm.lo);
@@ -439,9 +442,9 @@ __global__ void __launch_bounds__(256) __maxnreg__(kDfeoRegs<P1>) elem_dfeo_kern
         mw = fmaxf(mw, fabsf(wn.hi));
       }
       const float sd = splitter(9.0f * mw * mu);
-      SplitAcc acc(sd);
+      SplitAcc acc = SplitAcc::first(sd, w[0].hi, w[0].lo, u[0].hi, u[0].lo);
 #pragma unroll
-      for (int c8 = 0; c8 < 8; ++c8) acc.add(w[c8].hi, w[c8].lo, u[c8].hi, u[c8].lo);
+      for (int c8 = 1; c8 < 8; ++c8) acc.add(w[c8].hi, w[c8].lo, u[c8].hi, u[c8].lo);
       dot += df_to_f64(acc.result(sd));
     }
     dmask = dmask_next;
