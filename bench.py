@@ -298,6 +298,9 @@ def measure(pkg, args, mesh, arith, device, rank, world, dist, geom=0):
     elem_flops = elem_flops_dof * n_dofs
     elem_bytes = elem_bytes_dof * n_dofs
     name = ("fp64rc" if rc else "fp64") if arith == pkg.ARITH_FP64 else "df64"
+    pair_eo = arith != pkg.ARITH_FP64 and op.tile_info()[1] == 3  # even-odd pair kernel chosen
+    if pair_eo:
+        name = "df64eo"
     traffic = ncu_traffic(f"bk5_{name}_n{N}.md")
     if arith == pkg.ARITH_FP64:
         ach = elem_flops / (elem_ms * 1e-3) / 1e12
@@ -322,7 +325,9 @@ def measure(pkg, args, mesh, arith, device, rank, world, dist, geom=0):
         ach = elem_bytes / (elem_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / peaks["hbm_gbs"], "traffic": traffic,
-                "kernel": "elem_df_kernel (BK5, FP64-accurate FP32 pairs)", "peak_source": f"{peak_src} hbm_gbs",
+                "kernel": ("elem_dfeo_kernel (BK5, FP64-accurate FP32 pairs, even-odd)" if pair_eo
+                           else "elem_dfp_kernel (BK5, FP64-accurate FP32 pairs)"),
+                "peak_source": f"{peak_src} hbm_gbs",
                 "fp64_equiv_tflops": elem_flops / (elem_ms * 1e-3) / 1e12,
                 "fp32_peak_measured_tflops": fma["fp32_tflops"]}
     roof.update({"elem_ms": elem_ms, "update_ms": pinfo["kernel_ms"][1], "dir_ms": pinfo["kernel_ms"][2],
