@@ -37,6 +37,12 @@ namespace ceedbp {
 
 namespace {
 
+// G of the element staged in shared memory by asynchronous copies (p1 >= 12), or read from global
+// memory in the geometric stage after an L2 prefetch one element ahead (p1 <= 10: less than half
+// the shared memory per slot, so more warps per SM; measured faster at p1 = 8, slower at 12)
+template <int P1>
+constexpr bool kDfeoStageG = P1 >= 12;
+
 template <int P1>
 struct DfeoShape {
   static constexpr int H = P1 / 2, H3 = H * H * H, PP = P1 * P1, P3 = PP * P1;
@@ -44,7 +50,7 @@ struct DfeoShape {
   // of one pair per P1 lines spreads the lines a warp reads over distinct banks)
   static constexpr int HALF = (PP * H + P1 + 1) / 2 * 2;
   static constexpr int TILE = 6 * HALF;  // r+, r-, s+, s-, t+, t-
-  static constexpr int GSZ = 6 * P3;     // staged G of one element (pairs)
+  static constexpr int GSZ = kDfeoStageG<P1> ? 6 * P3 : 0;  // staged G of one element (pairs)
   static constexpr int USZ = 8 * H3;     // staged u of one element, [corner][octet] (8-byte cells)
   static constexpr int LSZ = 8 * H3;     // staged l2g of the next element, [corner][octet] (int32)
   static constexpr size_t SLOT_BYTES = sizeof(dfloat) * (TILE + GSZ + USZ) + sizeof(int) * ((LSZ + 3) / 4 * 4);
@@ -183,9 +189,20 @@ __global__ void __launch_bounds__(256) __maxnreg__(kDfeoRegs<P1>) elem_dfeo_kern
                                            : static_cast<const void*>(a.u_df + gg);
       cp_async8(sU + c8 * H3 + o, src);
     }
-    const float4* gsrc = reinterpret_cast<const float4*>(a.G + elem_of(s) * 6 * P3);
-    float4* gdst = reinterpret_cast<float4*>(sG);
-    for (int q = o; q < 3 * P3; q += H3) cp_async16(gdst + q, gsrc + q);
+    if constexpr (kDfeoStageG<P1>) {
+      const float4* gsrc = reinterpret_cast<const float4*>(a.G + elem_of(s) * 6 * P3);
+      float4* gdst = reinterpret_cast<float4*>(sG);
+      for (int q = o; q < 3 * P3; q += H3) cp_async16(gdst + q, gsrc + q);
+    }
+  };
+  // the element's G (48 p1^3 bytes) into L2 in 128-byte lines, issued after the geometric stage
+  // of the element before it (an element earlier measured slower at p1 = 8)
+  const auto prefetch_g = [&](int s) {
+    if constexpr (!kDfeoStageG<P1>) {
+      const char* gsrc = reinterpret_cast<const char*>(a.G + elem_of(s) * 6 * P3);
+      for (int q = o; q < 6 * P3 / 16; q += H3)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(gsrc + size_t(q) * 128));
+    }
   };
   const auto dir_bits = [&]() -> unsigned {
     unsigned dm = 0u;
@@ -201,6 +218,7 @@ __global__ void __launch_bounds__(256) __maxnreg__(kDfeoRegs<P1>) elem_dfeo_kern
     cp_async_commit();
     cp_async_wait_all();
     dmask = dir_bits();
+    prefetch_g(0);
     fetch_u_g(0);
   }
   cp_async_commit();
@@ -331,7 +349,14 @@ __global__ void __launch_bounds__(256) __maxnreg__(kDfeoRegs<P1>) elem_dfeo_kern
         const int ls = loc_s(c8), lt = loc_t(c8);
         dfloat g[6];
 #pragma unroll
-        for (int q = 0; q < 6; ++q) g[q] = sG[q * P3 + node];
+        for (int q = 0; q < 6; ++q) {
+          if constexpr (kDfeoStageG<P1>) {
+            g[q] = sG[q * P3 + node];
+          } else {
+            const float2 v = __ldg(reinterpret_cast<const float2*>(a.G + elem_of(s) * 6 * P3 + q * P3 + node));
+            g[q] = dfloat{v.x, v.y};
+          }
+        }
         const float gb = fmaxf(fmaxf(row_abs_sum3(g[0], g[1], g[2]), row_abs_sum3(g[1], g[3], g[4])),
                                row_abs_sum3(g[2], g[4], g[5]));
         const dfloat ur = X0[c8], us = X1[ls], ut = X2[lt];
@@ -364,6 +389,7 @@ __global__ void __launch_bounds__(256) __maxnreg__(kDfeoRegs<P1>) elem_dfeo_kern
     if (next_live) {
       cp_async_wait_all();  // its l2g
       dmask_next = dir_bits();
+      prefetch_g(s + 1);
       fetch_u_g(s + 1);
     }
     cp_async_commit();
