@@ -140,6 +140,15 @@ __global__ void __launch_bounds__(DfGlShape<P1, Q>::THREADS) elem_dfgl_kernel(co
   dfloat* sB = sA + Q3;
   dfloat* sC = sB + Q3;
   const int* l2g = m.l2g + e * P3;
+  if constexpr (KIND == kStiff) {
+    // the element's G (48 q^3 bytes) into L2 now, in 128-byte lines: the factor stage reads it
+    // after the gather and five line stages, from L2 instead of HBM
+    if (active) {
+      const char* gsrc = reinterpret_cast<const char*>(a.G + e * 6 * Q3);
+      for (int q = t; q < (48 * Q3 + 127) / 128; q += QQ)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(gsrc + size_t(q) * 128));
+    }
+  }
   if (active) {
     for (int idx = t; idx < P3; idx += QQ) {
       const int g = __ldg(l2g + idx);
