@@ -19,12 +19,15 @@
 // Thread mapping: one thread per mirror octet of nodes (i, j, k < p1/2), so
 // both outputs of every folded line product belong to the same thread (the
 // layout of elem_eo.cuh).  Schedule: each slot of p1^3/8 threads works through
-// a sequence of elements and fetches the next element's l2g, u and G by
+// a sequence of elements and fetches the next element's l2g and u by
 // asynchronous copies while it computes the current one (the dependent
-// l2g -> u gather and the G loads are off the critical path); the folded tiles
-// of the three directions go through shared memory; the fused (u, w) dot and
-// alpha are those of the direct pair kernels.  One component, even p1 (odd N),
-// p1 = 4 .. 12; not used for batched launches (block tables).
+// l2g -> u gather is off the critical path); the next element's G is
+// prefetched into L2 and read from global memory in the geometric stage
+// (p1 <= 10), or copied into shared memory with u (p1 = 12).  The folded tiles
+// of the three directions go through shared memory, and one loop body serves
+// the three directions; the fused (u, w) dot and alpha are those of the direct
+// pair kernels.  One component, even p1 (odd N), p1 = 4 .. 12; not used for
+// batched launches (block tables).
 #include <cuda_runtime.h>
 
 #include <type_traits>
