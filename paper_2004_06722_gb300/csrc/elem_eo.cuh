@@ -47,6 +47,22 @@ __device__ __forceinline__ int eo_node(int i, int j, int k, int bi, int bj, int 
   return ii + P1 * (jj + P1 * kk);
 }
 
+// One folded line product: S_E = sum_n E_n x+_n, then S_O accumulated on top of it, so that
+// y0 = S_E + S_O comes out of the chain and y1 = S_O - S_E = (S_E + S_O) - 2 S_E is one fma --
+// one FP64 operation fewer per output pair than summing S_E and S_O apart and combining them.
+template <int H>
+__device__ __forceinline__ void eo_pair(const double* E, const double* O, const double* xp, const double* xm,
+                                        double& y0, double& y1) {
+  double se = __dmul_rn(E[0], xp[0]);
+#pragma unroll
+  for (int n = 1; n < H; ++n) se = __fma_rn(E[n], xp[n], se);
+  double s = se;
+#pragma unroll
+  for (int n = 0; n < H; ++n) s = __fma_rn(O[n], xm[n], s);
+  y0 = s;
+  y1 = __fma_rn(-2.0, se, s);
+}
+
 // HELM: the Helmholtz term beta B u of Eq. (17) is compiled in only for beta != 0, so the plain
 // stiffness kernel carries no extra registers or branches.  BATCH: the block tables and per-problem
 // reductions of batched solves (one component), likewise compiled in only where used.
@@ -156,42 +172,30 @@ __global__ void elem_eo_kernel(const DeviceMesh m, const ElemArgs a, const int e
           const int jj = bj ? P1 - 1 - j : j, kk = bk ? P1 - 1 - k : k;
           const double* xp = Tc + 0 * HALF + rpos(jj, kk);
           const double* xm = Tc + 1 * HALF + rpos(jj, kk);
-          double se = 0.0, so = 0.0;
-#pragma unroll
-          for (int n = 0; n < H; ++n) {
-            se += sE[i * H + n] * xp[n];
-            so += sO[i * H + n] * xm[n];
-          }
-          gr[c][(bk << 2) | (bj << 1)] = se + so;
-          gr[c][(bk << 2) | (bj << 1) | 1] = so - se;
+          double y0, y1;
+          eo_pair<H>(sE + i * H, sO + i * H, xp, xm, y0, y1);
+          gr[c][(bk << 2) | (bj << 1)] = y0;
+          gr[c][(bk << 2) | (bj << 1) | 1] = y1;
         }
         {  // s: line (i', k'), output pair (j, p1-1-j)
           const int bi = q & 1, bk = q >> 1;
           const int ii = bi ? P1 - 1 - i : i, kk = bk ? P1 - 1 - k : k;
           const double* xp = Tc + 2 * HALF + spos(ii, kk);
           const double* xm = Tc + 3 * HALF + spos(ii, kk);
-          double se = 0.0, so = 0.0;
-#pragma unroll
-          for (int n = 0; n < H; ++n) {
-            se += sE[j * H + n] * xp[n];
-            so += sO[j * H + n] * xm[n];
-          }
-          gs[c][(bk << 2) | bi] = se + so;
-          gs[c][(bk << 2) | 2 | bi] = so - se;
+          double y0, y1;
+          eo_pair<H>(sE + j * H, sO + j * H, xp, xm, y0, y1);
+          gs[c][(bk << 2) | bi] = y0;
+          gs[c][(bk << 2) | 2 | bi] = y1;
         }
         {  // t: line (i', j'), output pair (k, p1-1-k)
           const int bi = q & 1, bj = q >> 1;
           const int ii = bi ? P1 - 1 - i : i, jj = bj ? P1 - 1 - j : j;
           const double* xp = Tc + 4 * HALF + tpos(ii, jj);
           const double* xm = Tc + 5 * HALF + tpos(ii, jj);
-          double se = 0.0, so = 0.0;
-#pragma unroll
-          for (int n = 0; n < H; ++n) {
-            se += sE[k * H + n] * xp[n];
-            so += sO[k * H + n] * xm[n];
-          }
-          gt[c][(bj << 1) | bi] = se + so;
-          gt[c][4 | (bj << 1) | bi] = so - se;
+          double y0, y1;
+          eo_pair<H>(sE + k * H, sO + k * H, xp, xm, y0, y1);
+          gt[c][(bj << 1) | bi] = y0;
+          gt[c][4 | (bj << 1) | bi] = y1;
         }
       }
     }
@@ -255,14 +259,10 @@ __global__ void elem_eo_kernel(const DeviceMesh m, const ElemArgs a, const int e
         const int jj = bj ? P1 - 1 - j : j, kk = bk ? P1 - 1 - k : k;
         const double* xp = Tc + 0 * HALF + rpos(jj, kk);
         const double* xm = Tc + 1 * HALF + rpos(jj, kk);
-        double se = 0.0, so = 0.0;
-#pragma unroll
-        for (int n = 0; n < H; ++n) {
-          se += sEt[i * H + n] * xp[n];
-          so += sOt[i * H + n] * xm[n];
-        }
-        w[(bk << 2) | (bj << 1)] = se + so;
-        w[(bk << 2) | (bj << 1) | 1] = so - se;
+        double y0, y1;
+        eo_pair<H>(sEt + i * H, sOt + i * H, xp, xm, y0, y1);
+        w[(bk << 2) | (bj << 1)] = y0;
+        w[(bk << 2) | (bj << 1) | 1] = y1;
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -270,14 +270,10 @@ __global__ void elem_eo_kernel(const DeviceMesh m, const ElemArgs a, const int e
         const int ii = bi ? P1 - 1 - i : i, kk = bk ? P1 - 1 - k : k;
         const double* xp = Tc + 2 * HALF + spos(ii, kk);
         const double* xm = Tc + 3 * HALF + spos(ii, kk);
-        double se = 0.0, so = 0.0;
-#pragma unroll
-        for (int n = 0; n < H; ++n) {
-          se += sEt[j * H + n] * xp[n];
-          so += sOt[j * H + n] * xm[n];
-        }
-        w[(bk << 2) | bi] += se + so;
-        w[(bk << 2) | 2 | bi] += so - se;
+        double y0, y1;
+        eo_pair<H>(sEt + j * H, sOt + j * H, xp, xm, y0, y1);
+        w[(bk << 2) | bi] += y0;
+        w[(bk << 2) | 2 | bi] += y1;
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -285,14 +281,10 @@ __global__ void elem_eo_kernel(const DeviceMesh m, const ElemArgs a, const int e
         const int ii = bi ? P1 - 1 - i : i, jj = bj ? P1 - 1 - j : j;
         const double* xp = Tc + 4 * HALF + tpos(ii, jj);
         const double* xm = Tc + 5 * HALF + tpos(ii, jj);
-        double se = 0.0, so = 0.0;
-#pragma unroll
-        for (int n = 0; n < H; ++n) {
-          se += sEt[k * H + n] * xp[n];
-          so += sOt[k * H + n] * xm[n];
-        }
-        w[(bj << 1) | bi] += se + so;
-        w[4 | (bj << 1) | bi] += so - se;
+        double y0, y1;
+        eo_pair<H>(sEt + k * H, sOt + k * H, xp, xm, y0, y1);
+        w[(bj << 1) | bi] += y0;
+        w[4 | (bj << 1) | bi] += y1;
       }
 #pragma unroll
       for (int c8 = 0; c8 < 8; ++c8) {
