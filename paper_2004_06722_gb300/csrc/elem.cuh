@@ -81,17 +81,19 @@ __device__ __forceinline__ void eo_mul(const double* T, const double (&x)[B], do
     xe[b] = x[b] + x[B - 1 - b];
     xo[b] = x[b] - x[B - 1 - b];
   }
+  // the odd half-sum accumulates on top of the even one: y[ra] = S_E + S_O leaves the chain and
+  // the mirror output is one fma of it (one FP64 operation fewer per output pair)
 #pragma unroll
   for (int ra = 0; ra < A / 2; ++ra) {
-    double se = 0.0, so = 0.0;
+    double se = 0.0;
 #pragma unroll
-    for (int b = 0; b < HB; ++b) {
-      se += TE[ra * HB + b] * xe[b];
-      so += TO[ra * HB + b] * xo[b];
-    }
+    for (int b = 0; b < HB; ++b) se += TE[ra * HB + b] * xe[b];
     if constexpr (B % 2 == 1) se += TM[ra] * x[B / 2];
-    y[ra] = se + so;
-    y[A - 1 - ra] = SIGN > 0 ? se - so : so - se;
+    double s = se;
+#pragma unroll
+    for (int b = 0; b < HB; ++b) s = __fma_rn(TO[ra * HB + b], xo[b], s);
+    y[ra] = s;                                                               // S_E + S_O
+    y[A - 1 - ra] = SIGN > 0 ? __fma_rn(2.0, se, -s) : __fma_rn(-2.0, se, s);  // S_E - S_O or S_O - S_E
   }
   if constexpr (A % 2 == 1) {
     constexpr int ra = A / 2;
